@@ -1,0 +1,252 @@
+"""FP64 CPU oracle (ctypes wrapper around oracle.c).
+
+TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and the CPU-baseline and
+reference legs of bench.py.  It shares no code with the CUDA library (`paper_1501_03879_gb300`)
+and never imports it.
+
+Functions mirror the passages of Chaudhury & Ramakrishnan (arXiv 1501.03879) cited in
+oracle.c: the closed-form prox (Sec. 2, Eq. closed-form), the conjugate prox (Eq. proxfstar),
+the box projection (Sec. 3), Algorithm 1 (EM-ADMM) and the NLEM driver (Sec. 3,
+Eq. L1regression).  Parity status of each function is listed in PINS below.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboracle.so")
+SRC = os.path.join(_HERE, "oracle.c")
+
+# every public function and what pins it (tests/test_oracle_*.py)
+PINS = {
+    "prox": "argmin of Eq. defprox by brute force (d=1,2), limits lam=0 / lam=inf, Moreau identity",
+    "prox_conj": "ball projection: norm <= lam, Moreau identity",
+    "project_box": "coordinate clamp, idempotent, nonexpansive",
+    "em_admm": "n=1, n=2, d=1 weighted median, planar Fermat point, brute-force grid, KKT, "
+               "Weiszfeld agreement, one step against numeric argmins of the augmented Lagrangian, "
+               "invariances",
+    "residuals": "r_pri / r_dual against their definitions on stored iterates (step-by-step replay)",
+    "nlem": "patch/weight assembly against numpy.pad reflect; constant image; S=1; k=1 weighted median",
+    "irls": "surrogate stationarity; converges to the EM within sqrt(eps)-scale",
+    "weiszfeld": "objective non-increasing; agrees with ADMM at convergence",
+}
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, FP64, no FMA contraction)."""
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", LIB_PATH, SRC, "-lm", "-lpthread"]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+    return LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(LIB_PATH)
+    D = ctypes.POINTER(ctypes.c_double)
+    F = ctypes.POINTER(ctypes.c_float)
+    I = ctypes.POINTER(ctypes.c_int)
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    c_int, c_double, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.orc_prox.argtypes = [D, D, c_double, c_int, D]
+    lib.orc_prox_conj.argtypes = [D, D, c_double, c_int, D]
+    lib.orc_project_box.argtypes = [D, c_int, c_double, c_double, D]
+    lib.orc_objective.argtypes = [D, D, D, c_int, c_int]
+    lib.orc_objective.restype = c_double
+    lib.orc_kkt_residual.argtypes = [D, D, D, c_int, c_int, c_double, c_double, c_double]
+    lib.orc_kkt_residual.restype = c_double
+    lib.orc_weighted_mean_start.argtypes = [D, D, c_int, c_int, c_double, c_double, D]
+    lib.orc_em_admm.argtypes = [D, D, c_int, c_int, c_double, c_double, c_double, c_int, D,
+                                c_double, c_int, D, I, D, D]
+    lib.orc_em_admm.restype = c_int
+    lib.orc_weiszfeld.argtypes = [D, D, c_int, c_int, D, c_int, D, D]
+    lib.orc_irls.argtypes = [D, D, c_int, c_int, c_double, c_double, D, c_double, c_int, D, D]
+    lib.orc_em_admm_batch.argtypes = [F, F, c_ll, c_int, c_int, c_double, c_double, c_double, c_int,
+                                      F, c_double, c_int, D, I, D, D, c_int]
+    lib.orc_em_admm_batch.restype = c_int
+    lib.orc_nlem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_double, c_int, c_double,
+                             c_double, c_double, c_int, c_int, c_int, LL, c_ll, D, I, D, D, I, D, c_int]
+    lib.orc_nlem.restype = c_int
+    lib.orc_nlem_problem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_ll, c_int, D, D, D]
+    lib.orc_nlem_problem.restype = c_int
+    lib.orc_num_cores.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def num_cores() -> int:
+    return int(_load().orc_num_cores())
+
+
+def prox(v, u, lam):
+    """Eq. (closed-form): Psi_lam(v, u)."""
+    v, u = _f64(v), _f64(u)
+    out = np.empty_like(v)
+    _load().orc_prox(_dp(v), _dp(u), float(lam), v.size, _dp(out))
+    return out
+
+
+def prox_conj(v, u, lam):
+    """Eq. (proxfstar): projection of v - u onto the ball of radius lam."""
+    v, u = _f64(v), _f64(u)
+    out = np.empty_like(v)
+    _load().orc_prox_conj(_dp(v), _dp(u), float(lam), v.size, _dp(out))
+    return out
+
+
+def project_box(x, lo, hi):
+    x = _f64(x)
+    out = np.empty_like(x)
+    _load().orc_project_box(_dp(x), x.size, float(lo), float(hi), _dp(out))
+    return out
+
+
+def objective(z, pts, w):
+    """Eq. (1) objective sum_k w_k ||z - a_k||."""
+    z, pts, w = _f64(z), _f64(pts), _f64(w)
+    n, d = pts.shape
+    return float(_load().orc_objective(_dp(z), _dp(pts), _dp(w), n, d))
+
+
+def kkt_residual(z, pts, w, lo, hi, tau=None):
+    z, pts, w = _f64(z), _f64(pts), _f64(w)
+    n, d = pts.shape
+    if tau is None:
+        tau = 1e-9 * max(1.0, abs(hi - lo))
+    return float(_load().orc_kkt_residual(_dp(z), _dp(pts), _dp(w), n, d, float(lo), float(hi), float(tau)))
+
+
+def weighted_mean_start(pts, w, lo, hi):
+    pts, w = _f64(pts), _f64(w)
+    n, d = pts.shape
+    z = np.empty(d)
+    _load().orc_weighted_mean_start(_dp(pts), _dp(w), n, d, float(lo), float(hi), _dp(z))
+    return z
+
+
+def em_admm(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1):
+    """Algorithm 1 on one problem.  Returns (z, iters_used, r_pri, r_dual)."""
+    pts, w = _f64(pts), _f64(w)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    n, d = pts.shape
+    z = np.empty(d)
+    used = np.zeros(1, dtype=np.int32)
+    rp = np.zeros(1)
+    rd = np.zeros(1)
+    z0a = _f64(z0) if z0 is not None else None
+    rc = _load().orc_em_admm(_dp(pts), _dp(w), n, d, float(lo), float(hi), float(mu), int(iters),
+                             _dp(z0a), float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd))
+    if rc != 0:
+        raise MemoryError("oracle em_admm out of memory")
+    return z, int(used[0]), float(rp[0]), float(rd[0])
+
+
+def weiszfeld(pts, w, x0, iters):
+    pts, w, x0 = _f64(pts), _f64(w), _f64(x0)
+    n, d = pts.shape
+    x = np.empty(d)
+    F = np.empty(max(iters, 1))
+    _load().orc_weiszfeld(_dp(pts), _dp(w), n, d, _dp(x0), int(iters), _dp(x), _dp(F))
+    return x, F[:iters]
+
+
+def irls(pts, w, lo, hi, x0, eps, iters):
+    pts, w, x0 = _f64(pts), _f64(w), _f64(x0)
+    n, d = pts.shape
+    x = np.empty(d)
+    F = np.empty(max(iters, 1))
+    _load().orc_irls(_dp(pts), _dp(w), n, d, float(lo), float(hi), _dp(x0), float(eps), int(iters), _dp(x), _dp(F))
+    return x, F[:iters]
+
+
+def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nthreads=0):
+    """Algorithm 1 on a float32 batch [B, n, d] (threads over problems).
+    Returns (z [B,d] float64, iters_used [B], r_pri [B], r_dual [B])."""
+    pts = np.ascontiguousarray(pts, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    B, n, d = pts.shape
+    z = np.empty((B, d))
+    used = np.zeros(B, dtype=np.int32)
+    rp = np.zeros(B)
+    rd = np.zeros(B)
+    z0a = np.ascontiguousarray(z0, dtype=np.float32) if z0 is not None else None
+    rc = _load().orc_em_admm_batch(_fp(pts), _fp(w), B, n, d, float(lo), float(hi), float(mu), int(iters),
+                                   _fp(z0a), float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd),
+                                   int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle em_admm_batch failed")
+    return z, used, rp, rd
+
+
+def nlem(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init_mode=0,
+         weight_mode=0, pixels=None, nthreads=0):
+    """NLEM (Sec. 3) on a float32 image.  Returns a dict with out (float64), iters_used,
+    r_pri, r_dual, n (points per problem) and wsum (sum of weights), one entry per processed
+    pixel (all pixels row-major, or the listed linear indices)."""
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    H, W = img.shape
+    if pixels is None:
+        npix = H * W
+        pix = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64).reshape(-1))
+        npix = pix.size
+    out = np.empty(npix)
+    used = np.zeros(npix, dtype=np.int32)
+    rp = np.zeros(npix)
+    rd = np.zeros(npix)
+    nn = np.zeros(npix, dtype=np.int32)
+    ws = np.zeros(npix)
+    pixp = pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None
+    rc = _load().orc_nlem(_fp(img), H, W, int(k), int(S), float(h), float(mu), int(iters), float(lo), float(hi),
+                          float(tol), int(check_every), int(init_mode), int(weight_mode), pixp, npix,
+                          _dp(out), _ip(used), _dp(rp), _dp(rd), _ip(nn), _dp(ws), int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle nlem failed")
+    res = dict(out=out, iters_used=used, r_pri=rp, r_dual=rd, n=nn, wsum=ws)
+    if pixels is None:
+        for key in ("out", "iters_used", "r_pri", "r_dual", "n", "wsum"):
+            res[key] = res[key].reshape(H, W)
+    return res
+
+
+def nlem_problem(img, k, S, h, lin, weight_mode=0):
+    """(points [n, k*k], weights [n], centre patch) that NLEM builds for pixel `lin`."""
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    H, W = img.shape
+    d = k * k
+    pts = np.zeros((S * S, d))
+    w = np.zeros(S * S)
+    pc = np.zeros(d)
+    n = _load().orc_nlem_problem(_fp(img), H, W, int(k), int(S), float(h), int(lin), int(weight_mode),
+                                 _dp(pts), _dp(w), _dp(pc))
+    return pts[:n].copy(), w[:n].copy(), pc

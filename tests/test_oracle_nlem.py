@@ -1,0 +1,117 @@
+"""Pins for the oracle's NLEM driver (Sec. 3) and for the seeded input generators (CPU only)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 seeded with 1234567 (reference output of the published generator)
+    got = synth.draw_u64(np.uint64(1234567), np.arange(5))
+    assert got.tolist() == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                            4593380528125082431, 16408922859458223821]
+
+
+def test_generators_are_counter_based():
+    full = synth.em_points(7, np.arange(6), 13, 5)
+    part = synth.em_points(7, [4, 1], 13, 5)
+    assert np.array_equal(full[[4, 1]], part)
+    w = synth.em_weights(7, np.arange(6), 13)
+    assert np.array_equal(w[[5, 2]], synth.em_weights(7, [5, 2], 13))
+    assert np.all(w > 0)
+    pts = synth.em_points(3, np.arange(200), 50, 7)
+    out = np.all((pts == 0) | (pts == 255), axis=2)
+    assert 0.07 < out.mean() < 0.13                      # ~10% whole-point outliers
+    assert pts.min() >= 0 and pts.max() <= 255
+    g1, f1 = synth.noisy_image(5, 40, 30, 20.0)
+    g2, _ = synth.noisy_image(5, 40, 30, 20.0)
+    assert np.array_equal(g1, g2) and g1.dtype == np.float32
+    assert 15 < np.std(g1 - f1) < 25
+
+
+def _reflect_patches(img, k):
+    r = (k - 1) // 2
+    P = np.pad(img.astype(np.float64), r, mode="reflect")
+    H, W = img.shape
+    return lambda i, j: P[i:i + k, j:j + k].reshape(-1)
+
+
+@pytest.mark.parametrize("k,S", [(3, 5), (7, 11), (5, 7)])
+def test_problem_assembly(k, S):
+    g, _ = synth.noisy_image(21, 23, 19, 20.0)
+    H, W = g.shape
+    patch = _reflect_patches(g, k)
+    h = 200.0
+    R = (S - 1) // 2
+    for lin in (0, W - 1, (H // 2) * W + W // 2, H * W - 1, 3 * W + 1):
+        pts, w, pc = oracle.nlem_problem(g, k, S, h, lin)
+        i, j = divmod(lin, W)
+        assert np.array_equal(pc, patch(i, j))
+        exp_pts = [patch(a, b) for a in range(max(0, i - R), min(H, i + R + 1))
+                   for b in range(max(0, j - R), min(W, j + R + 1))]
+        assert len(pts) == len(exp_pts)
+        assert np.array_equal(pts, np.array(exp_pts))
+        self_idx = [t for t, p in enumerate(pts) if np.array_equal(p, pc)]
+        assert any(abs(w[t] - 1.0) < 1e-15 for t in self_idx)        # w_ii = exp(0) = 1
+        assert np.all((w > 0) & (w <= 1))
+    # corner window holds ((S+1)/2)^2 centres, interior S^2
+    assert len(oracle.nlem_problem(g, k, S, h, 0)[1]) == ((S + 1) // 2) ** 2
+
+
+def test_bf16_weight_model_error_bound():
+    g, _ = synth.noisy_image(22, 30, 30, 30.0, salt_pepper=0.05)
+    for lin in (0, 455, 899):
+        p0, w0, pc = oracle.nlem_problem(g, 9, 7, 300.0, lin, weight_mode=0)
+        p1, w1, _ = oracle.nlem_problem(g, 9, 7, 300.0, lin, weight_mode=1)
+        D0 = -np.log(w0) * 300.0 ** 2
+        D1 = -np.log(w1) * 300.0 ** 2
+        # bf16 keeps 8 significant bits: each product is off by at most ~2^-8 relative
+        bound = 2 * np.sum(np.abs(pc)[None, :] * np.abs(p0), axis=1) * 2.0 ** -7 + 1e-6
+        assert np.all(np.abs(D1 - D0) <= bound)
+
+
+def test_constant_image():
+    for c in (0.0, 37.5, 255.0):
+        g = np.full((12, 13), c, dtype=np.float32)
+        r = oracle.nlem(g, 3, 5, 100.0, 1.0, 20)
+        assert np.allclose(r["out"], c, atol=1e-12)
+    g = np.full((9, 9), 300.0, dtype=np.float32)
+    assert np.allclose(oracle.nlem(g, 3, 5, 100.0, 1.0, 20)["out"], 255.0)
+
+
+def test_window_one_gives_clamped_input():
+    g, _ = synth.noisy_image(23, 15, 17, 40.0)
+    r = oracle.nlem(g, 5, 1, 400.0, 1.0, 10)
+    assert np.allclose(r["out"], np.clip(g, 0, 255), atol=1e-12)
+    assert np.all(r["n"] == 1)
+
+
+def test_patch_one_is_weighted_scalar_median():
+    g, _ = synth.noisy_image(24, 14, 11, 20.0)
+    H, W = g.shape
+    S, h = 5, 60.0
+    r = oracle.nlem(g, 1, S, h, 0.02, 6000)
+    R = 2
+    for lin in range(0, H * W, 7):
+        i, j = divmod(lin, W)
+        vals = g[max(0, i - R):i + R + 1, max(0, j - R):j + R + 1].astype(np.float64).reshape(-1)
+        w = np.exp(-(vals - float(g[i, j])) ** 2 / h ** 2)
+        F = lambda t: float(np.sum(w * np.abs(t - vals)))
+        cand = np.clip(vals, 0, 255)
+        Fstar = min(F(t) for t in cand)                   # a weighted median is a data point
+        assert F(r["out"][i, j]) <= Fstar * (1 + 1e-9) + 1e-9
+
+
+def test_nlem_denoises_synthetic_image():
+    g, f = synth.noisy_image(25, 48, 48, 20.0)
+    r = oracle.nlem(g, 7, 11, 200.0, 1e-3, 4, init_mode=1)
+    assert synth.psnr(r["out"], f) > synth.psnr(g, f) + 4.0
+
+
+def test_pixel_subset_matches_full():
+    g, _ = synth.noisy_image(26, 20, 20, 20.0)
+    full = oracle.nlem(g, 5, 7, 200.0, 1.0, 15)
+    pix = [0, 21, 399, 200]
+    sub = oracle.nlem(g, 5, 7, 200.0, 1.0, 15, pixels=pix)
+    assert np.array_equal(sub["out"], full["out"].reshape(-1)[pix])

@@ -1,0 +1,360 @@
+"""Pins for the FP64 oracle: facts fixed by the paper and by mathematics, independent of the
+oracle's own code (CPU only)."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize, minimize_scalar
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------
+# prox map (Sec. 2, Eqs. defprox, closed-form, proxfstar, MD)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lam", [0.0, 0.3, 1.0, 2.5, 7.0])
+def test_prox_matches_argmin_1d(lam):
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        v, u = rng.normal(size=1) * 3, rng.normal(size=1) * 3
+        res = minimize_scalar(lambda x: lam * abs(x - u[0]) + 0.5 * (x - v[0]) ** 2,
+                              bounds=(-50, 50), method="bounded", options={"xatol": 1e-12})
+        assert abs(oracle.prox(v, u, lam)[0] - res.x) < 1e-7
+
+
+@pytest.mark.parametrize("lam", [0.2, 1.0, 4.0])
+def test_prox_matches_argmin_2d(lam):
+    rng = np.random.default_rng(2)
+    for _ in range(8):
+        v, u = rng.normal(size=2) * 2, rng.normal(size=2) * 2
+        obj = lambda x: lam * np.linalg.norm(x - u) + 0.5 * np.sum((x - v) ** 2)
+        best = None
+        for x0 in (v, u, 0.5 * (u + v)):
+            r = minimize(obj, x0, method="Nelder-Mead", options={"xatol": 1e-11, "fatol": 1e-14, "maxiter": 20000})
+            if best is None or r.fun < best.fun:
+                best = r
+        p = oracle.prox(v, u, lam)
+        assert obj(p) <= best.fun + 1e-10
+        assert np.linalg.norm(p - best.x) < 1e-5
+
+
+def test_prox_limits_and_moreau():
+    rng = np.random.default_rng(3)
+    for d in (1, 3, 49):
+        v, u = rng.normal(size=d) * 5, rng.normal(size=d) * 5
+        assert np.allclose(oracle.prox(v, u, 0.0), v)                 # lam = 0 gives v
+        assert np.allclose(oracle.prox(v, u, 1e300), u)               # lam = inf gives u
+        for lam in (0.1, 1.0, 10.0, 100.0):
+            p, pc = oracle.prox(v, u, lam), oracle.prox_conj(v, u, lam)
+            assert np.allclose(p + pc, v, atol=1e-12)                 # Moreau decomposition (MD)
+            assert np.linalg.norm(pc) <= lam * (1 + 1e-12)            # inside the lam-ball (CF)
+    # zero distance: the argmin is v itself
+    v = np.array([1.0, 2.0])
+    assert np.array_equal(oracle.prox(v, v, 3.0), v)
+
+
+def test_box_projection():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=100) * 200 + 100
+    p = oracle.project_box(x, 0.0, 255.0)
+    assert np.array_equal(p, np.clip(x, 0.0, 255.0))
+    assert np.array_equal(oracle.project_box(p, 0.0, 255.0), p)       # idempotent
+    y = rng.normal(size=100) * 200 + 100
+    assert np.linalg.norm(oracle.project_box(y, 0, 255) - p) <= np.linalg.norm(y - x) + 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 1: hand-worked iterations, and one step from the augmented Lagrangian
+# ---------------------------------------------------------------------------------------
+
+def test_alg1_hand_worked_example():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "alg1_worked_example.txt"))
+            if l.strip() and not l.startswith("#")]
+    pts = np.array([[0.0], [10.0]])
+    w = np.array([3.0, 1.0])
+    for it, z_ref, rp_ref, rd_ref in rows:
+        z, used, rp, rd = oracle.em_admm(pts, w, 0.0, 10.0, 1.0, int(it))
+        assert used == int(it)
+        assert abs(z[0] - z_ref) < 1e-14
+        assert abs(rp - rp_ref) < 1e-14
+        assert abs(rd - rd_ref) < 1e-14
+
+
+def _lagrangian_steps(pts, w, lo, hi, mu, z, y, steps):
+    """ADMM steps taken directly from the augmented Lagrangian of Sec. 2 by numerical
+    minimisation (Gauss-Seidel over x_k then z, then the multiplier rule)."""
+    n, d = pts.shape
+    for _ in range(steps):
+        x = np.zeros_like(pts)
+        for k in range(n):
+            f = lambda xx: (w[k] * np.linalg.norm(xx - pts[k]) + (xx - z) @ y[k]
+                            + 0.5 * mu * np.sum((xx - z) ** 2))
+            best = None
+            for x0 in (z, pts[k], z - y[k] / mu):
+                r = minimize(f, x0, method="Nelder-Mead",
+                             options={"xatol": 1e-12, "fatol": 1e-15, "maxiter": 40000})
+                if best is None or r.fun < best.fun:
+                    best = r
+            x[k] = best.x
+        g = lambda zz: sum(y[k] @ (x[k] - zz) + 0.5 * mu * np.sum((x[k] - zz) ** 2) for k in range(n))
+        r = minimize(g, np.clip(z, lo, hi), method="L-BFGS-B", bounds=[(lo, hi)] * d,
+                     options={"ftol": 1e-16, "gtol": 1e-12})
+        z = r.x
+        y = y + mu * (x - z)
+    return z
+
+
+def test_alg1_steps_match_augmented_lagrangian():
+    pts = np.array([[0.0, 0.0], [4.0, 1.0], [1.0, 5.0], [6.0, 6.0]])
+    w = np.array([1.0, 0.7, 1.3, 0.4])
+    lo, hi, mu = 0.5, 5.0, 0.8
+    z0 = oracle.weighted_mean_start(pts, w, lo, hi)
+    for steps in (1, 2, 3):
+        z_ref = _lagrangian_steps(pts, w, lo, hi, mu, z0.copy(), np.zeros_like(pts), steps)
+        z, *_ = oracle.em_admm(pts, w, lo, hi, mu, steps)
+        assert np.linalg.norm(z - z_ref) < 1e-5, (steps, z, z_ref)
+
+
+# ---------------------------------------------------------------------------------------
+# closed forms of problem (1)
+# ---------------------------------------------------------------------------------------
+
+def _converged(pts, w, lo, hi, mu=None, iters=20000):
+    if mu is None:
+        mu = 1e-2 * max(np.sum(w), 1e-12) / len(w)
+    return oracle.em_admm(pts, w, lo, hi, mu, iters)[0]
+
+
+def test_single_point_is_its_projection():
+    rng = np.random.default_rng(6)
+    for d in (1, 4, 49):
+        a = rng.uniform(-100, 400, size=(1, d))
+        z = _converged(a, np.array([2.0]), 0.0, 255.0, mu=1.0, iters=200)
+        assert np.allclose(z, np.clip(a[0], 0, 255), atol=1e-9)
+
+
+def test_two_points_heavier_wins():
+    rng = np.random.default_rng(7)
+    for d in (1, 3, 25):
+        a = rng.uniform(10, 240, size=(2, d))
+        z = _converged(a, np.array([1.5, 1.0]), 0.0, 255.0, mu=0.05, iters=5000)
+        assert np.linalg.norm(z - a[0]) < 1e-7
+
+
+def _weighted_median_interval(x, w):
+    o = np.argsort(x)
+    xs, ws = x[o], w[o]
+    c = np.cumsum(ws)
+    half = 0.5 * c[-1]
+    i = int(np.searchsorted(c, half - 1e-15 * c[-1]))
+    if abs(c[i] - half) <= 1e-12 * c[-1] and i + 1 < len(xs):
+        return xs[i], xs[i + 1]
+    return xs[i], xs[i]
+
+
+def test_d1_is_weighted_scalar_median():
+    rng = np.random.default_rng(8)
+    for trial in range(20):
+        n = int(rng.integers(1, 12))
+        x = rng.uniform(-50, 300, n)
+        w = rng.uniform(0.1, 3.0, n)
+        lo, hi = 0.0, 255.0
+        z = _converged(x[:, None], w, lo, hi, mu=0.01 * w.mean(), iters=20000)[0]
+        a, b = _weighted_median_interval(x, w)
+        a, b = min(max(a, lo), hi), min(max(b, lo), hi)
+        F = lambda t: float(np.sum(w * np.abs(t - x)))
+        assert a - 1e-6 <= z <= b + 1e-6, (z, a, b)
+        assert F(z) <= F(a) + 1e-7 * F(a)
+
+
+def _fermat_point(A, B, C):
+    """Fermat point of a triangle with all angles < 120 deg: intersection of the lines joining
+    each vertex to the apex of the equilateral triangle erected outward on the opposite side."""
+    def apex(P, Q, R):   # apex on side PQ, away from R
+        m = 0.5 * (P + Q)
+        t = np.array([-(Q - P)[1], (Q - P)[0]]) * (math.sqrt(3) / 2)
+        c1, c2 = m + t, m - t
+        return c1 if np.linalg.norm(c1 - R) > np.linalg.norm(c2 - R) else c2
+    A1, B1 = apex(B, C, A), apex(C, A, B)
+    M = np.array([A1 - A, -(B1 - B)]).T
+    s = np.linalg.solve(M, B - A)
+    return A + s[0] * (A1 - A)
+
+
+def test_planar_fermat_point_embedded():
+    rng = np.random.default_rng(9)
+    found = 0
+    while found < 6:
+        T = rng.uniform(-5, 5, size=(3, 2))
+        angs = []
+        for i in range(3):
+            u, v = T[(i + 1) % 3] - T[i], T[(i + 2) % 3] - T[i]
+            angs.append(math.degrees(math.acos(u @ v / np.linalg.norm(u) / np.linalg.norm(v))))
+        if max(angs) >= 115:
+            continue
+        found += 1
+        F2 = _fermat_point(*T)
+        d = 6
+        Q, _ = np.linalg.qr(rng.normal(size=(d, 2)))        # random orthonormal 2-frame in R^6
+        off = rng.uniform(-1, 1, d)
+        pts = T @ Q.T + off
+        z = _converged(pts, np.ones(3), -1e3, 1e3, mu=0.02, iters=20000)
+        assert np.linalg.norm(z - (F2 @ Q.T + off)) < 1e-6
+
+
+def test_obtuse_triangle_gives_vertex():
+    T = np.array([[0.0, 0.0], [10.0, 0.0], [5.0, 0.8]])      # angle at the third vertex > 120 deg
+    z = _converged(T, np.ones(3), -1e3, 1e3, mu=0.02, iters=20000)
+    assert np.linalg.norm(z - T[2]) < 1e-7
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_grid(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 7))
+    d = 1 + seed % 2
+    pts = rng.uniform(-2, 12, (n, d))
+    w = rng.uniform(0.2, 2.0, n)
+    lo, hi = 0.0, 10.0
+    z = _converged(pts, w, lo, hi, mu=0.02, iters=30000)
+    delta = 0.01 if d == 2 else 0.0005
+    g = np.arange(lo, hi + delta / 2, delta)
+    grid = np.stack(np.meshgrid(*([g] * d), indexing="ij"), -1).reshape(-1, d)
+    F = np.sum(w[None, :] * np.linalg.norm(grid[:, None, :] - pts[None, :, :], axis=2), axis=1)
+    fmin = F.min()
+    fz = oracle.objective(z, pts, w)
+    assert fmin - w.sum() * delta * math.sqrt(d) / 2 - 1e-9 <= fz <= fmin + 1e-9
+    assert np.all(z >= lo - 1e-12) and np.all(z <= hi + 1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# "minimiser = projection of the EM" (Sec. 1) holds in d = 1 and when the EM is in C, and
+# fails in general for d >= 2
+# ---------------------------------------------------------------------------------------
+
+def test_projection_claim_d1():
+    rng = np.random.default_rng(11)
+    for _ in range(10):
+        n = int(rng.integers(2, 9))
+        x = rng.uniform(-100, 400, (n, 1))
+        w = rng.uniform(0.1, 2, n)
+        em = _converged(x, w, -1e4, 1e4, mu=0.01 * w.mean(), iters=20000)
+        zc = _converged(x, w, 0.0, 255.0, mu=0.01 * w.mean(), iters=20000)
+        F = lambda t: oracle.objective(t, x, w)
+        assert F(zc) <= F(np.clip(em, 0, 255)) + 1e-7 * F(zc)
+        assert F(np.clip(em, 0, 255)) <= F(zc) + 1e-6 * F(zc)
+
+
+def test_projection_claim_interior():
+    rng = np.random.default_rng(12)
+    pts = rng.uniform(50, 200, (9, 5))
+    w = rng.uniform(0.5, 1.5, 9)
+    em = _converged(pts, w, -1e4, 1e4, mu=0.05, iters=20000)
+    assert np.all((em > 0) & (em < 255))
+    zc = _converged(pts, w, 0.0, 255.0, mu=0.05, iters=20000)
+    assert np.linalg.norm(zc - em) < 1e-6
+
+
+def test_projection_claim_counterexample():
+    pts = np.array([[-1.4, 0.5], [1.3, -2.5], [3.6, 1.2]])
+    w = np.array([0.7, 1.3, 1.9])
+    em = _converged(pts, w, -1e6, 1e6, mu=1e-3, iters=40000)
+    zc = _converged(pts, w, 0.0, 1.0, mu=1e-3, iters=40000)
+    assert np.allclose(em, [3.6, 1.2], atol=1e-7)          # the EM sits on the heaviest point
+    Fp = oracle.objective(np.clip(em, 0, 1), pts, w)
+    Fc = oracle.objective(zc, pts, w)
+    assert Fc < Fp - 0.5                                    # projecting the EM is not optimal
+    assert oracle.kkt_residual(zc, pts, w, 0.0, 1.0) < 1e-8
+
+
+# ---------------------------------------------------------------------------------------
+# optimality and comparison with Weiszfeld / IRLS
+# ---------------------------------------------------------------------------------------
+
+def test_kkt_at_converged_solution():
+    rng = np.random.default_rng(13)
+    for d, n in ((2, 5), (7, 30), (49, 60)):
+        pts = rng.uniform(0, 255, (n, d))
+        w = rng.exponential(1.0, n)
+        z = _converged(pts, w, 0.0, 255.0, mu=0.005 * w.mean(), iters=20000)
+        assert oracle.kkt_residual(z, pts, w, 0.0, 255.0) < 1e-6
+
+
+def test_weiszfeld_monotone_and_admm_not_worse():
+    rng = np.random.default_rng(14)
+    for d, n in ((2, 6), (5, 12), (25, 40)):
+        pts = rng.normal(size=(n, d)) * 10
+        w = rng.uniform(0.2, 2, n)
+        x0 = pts.mean(0) + 0.37
+        xw, F = oracle.weiszfeld(pts, w, x0, 400)
+        assert np.all(np.diff(F) <= 1e-12 * F[0])           # Weiszfeld never increases F
+        z = _converged(pts, w, -1e6, 1e6, mu=0.01, iters=20000)
+        Fz = oracle.objective(z, pts, w)
+        assert Fz <= F[-1] + 1e-9 * Fz
+        assert np.linalg.norm(z - xw) < 1e-4 * (1 + np.linalg.norm(z))
+
+
+def test_irls_surrogate_close_to_em():
+    rng = np.random.default_rng(15)
+    pts = rng.uniform(0, 255, (30, 9))
+    w = rng.uniform(0.1, 1, 30)
+    eps = 1e-6
+    x, F = oracle.irls(pts, w, -1e6, 1e6, pts.mean(0), eps, 3000)
+    z = _converged(pts, w, -1e6, 1e6, mu=0.01, iters=20000)
+    Fz = oracle.objective(z, pts, w)
+    assert abs(F[-1] - Fz) <= math.sqrt(eps) * w.sum() + 1e-9 * Fz
+    # the surrogate (2) decreases along the IRLS iterates (majorise-minimise)
+    xs = pts.mean(0)
+    prev = np.inf
+    for it in range(20):
+        xs, _ = oracle.irls(pts, w, -1e6, 1e6, xs, eps, 1)
+        Fe = float(np.sum(w * np.sqrt(np.sum((xs - pts) ** 2, 1) + eps)))
+        assert Fe <= prev + 1e-9 * Fe
+        prev = Fe
+
+
+# ---------------------------------------------------------------------------------------
+# invariances of Algorithm 1 (iterates, not only the limit)
+# ---------------------------------------------------------------------------------------
+
+def test_invariances():
+    rng = np.random.default_rng(16)
+    pts = rng.uniform(0, 255, (40, 9))
+    w = rng.exponential(1.0, 40)
+    mu, T = 0.7, 37
+    z, *_ = oracle.em_admm(pts, w, 0.0, 255.0, mu, T)
+    perm = rng.permutation(40)
+    zp, *_ = oracle.em_admm(pts[perm], w[perm], 0.0, 255.0, mu, T)
+    assert np.allclose(z, zp, rtol=0, atol=1e-9)
+    za, *_ = oracle.em_admm(pts, 3.0 * w, 0.0, 255.0, 3.0 * mu, T)       # (w, mu) -> (aw, a mu)
+    assert np.allclose(z, za, rtol=0, atol=1e-9)
+    zs, *_ = oracle.em_admm(2.0 * pts, w, 0.0, 510.0, mu / 2.0, T)       # (a, C, mu) -> (sa, sC, mu/s)
+    assert np.allclose(2.0 * z, zs, rtol=0, atol=1e-9)
+
+
+def test_iters_zero_returns_projected_weighted_mean():
+    rng = np.random.default_rng(17)
+    pts = rng.uniform(-50, 300, (11, 4))
+    w = rng.uniform(0.1, 1, 11)
+    z, used, rp, rd = oracle.em_admm(pts, w, 0.0, 255.0, 1.0, 0)
+    assert used == 0
+    assert np.allclose(z, np.clip((w[:, None] * pts).sum(0) / w.sum(), 0, 255), atol=1e-12)
+
+
+def test_tolerance_stopping_rule():
+    rng = np.random.default_rng(18)
+    pts = rng.uniform(0, 255, (50, 9))
+    w = rng.exponential(1.0, 50)
+    z, used, rp, rd = oracle.em_admm(pts, w, 0.0, 255.0, 0.01, 500, tol=1e-4, check_every=5)
+    assert used % 5 == 0 and used < 500
+    assert rp < 1e-4 and rd < 1e-4
+    # the previous check point had not met the rule
+    _, _, rp0, rd0 = oracle.em_admm(pts, w, 0.0, 255.0, 0.01, used - 5)
+    assert not (rp0 < 1e-4 and rd0 < 1e-4)
+    # fixed count: same iterate as tol-mode at that count
+    zf, usedf, _, _ = oracle.em_admm(pts, w, 0.0, 255.0, 0.01, used)
+    assert usedf == used and np.array_equal(zf, z)
