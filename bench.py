@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the NLEM / EM-ADMM hot path on GB300.
+
+One step = one pass over the production workload:
+  * NLEM denoising of three 512x512 synthetic images (sigma = 10, 20, 40), 7x7 patches
+    (d = 49), 21x21 search window (n <= 441, clipped at the border), h = 10*sigma, box
+    [0, 255], rho = 1, stop at relative primal/dual residual < 1e-4 checked every 10
+    iterations, cap 300, weighted-mean start;
+  * a standalone em_solve_batch of 262144 problems, n = 441, d = 49, points uniform on
+    [0, 255] with 10% whole-point outliers at 255*Bernoulli(1/2), weights Exp(1), same
+    stopping rule.
+Every pixel and every standalone problem is one EM solve; `value` is EM solves per second
+over the whole step (inputs resident in HBM), `mpixel_per_s` the NLEM part alone.
+
+--impl reference times the FP64 CPU oracle (the method's plain restatement) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIGMAS = (10.0, 20.0, 40.0)
+H = W = 512
+K_PATCH, S_WIN = 7, 21
+RHO, TOL, CHECK, CAP = 1.0, 1e-4, 10, 300
+EM_B, EM_N, EM_D = 262144, 441, 49
+BOX = (0.0, 255.0)
+SEED = 1001                     # workload seed (configuration index 1)
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
+
+METRIC = "EM solves/s (NLEM Mpixel/s alongside) at relative residual 1e-4 (cap 300) vs FP64 oracle; % of roofline"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--em-batch", type=int, default=EM_B, help="standalone problems per step (default 262144)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work (one convention for every report):
+#   per (problem, iteration): 8*n*d + 4*n FP32 flops
+#   per NLEM pixel once: 3*n*d (distances) + 2*n*d (weighted mean) + 3*n (exp)
+#   per standalone problem once: 2*n*d (weighted mean)
+# ------------------------------------------------------------------------------------------
+def window_counts(Hh, Ww, S):
+    R = (S - 1) // 2
+    r = np.arange(Hh)
+    c = np.arange(Ww)
+    nr = np.minimum(r + R, Hh - 1) - np.maximum(r - R, 0) + 1
+    nc = np.minimum(c + R, Ww - 1) - np.maximum(c - R, 0) + 1
+    return (nr[:, None] * nc[None, :]).astype(np.float64)
+
+
+def nlem_flops(n_map, iters_map, d):
+    return float(np.sum((8.0 * n_map * d + 4.0 * n_map) * iters_map + 5.0 * n_map * d + 3.0 * n_map))
+
+
+def em_flops(iters, n, d):
+    return float(np.sum((8.0 * n * d + 4.0 * n) * iters.astype(np.float64) + 2.0 * n * d))
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------
+def cpu_sample_rate(seconds):
+    """EM solves/s of the oracle (all host cores) on a bounded sample: NLEM pixels of the
+    sigma=20 image and standalone problems, in the step's proportion (3 images : 1 batch of
+    equal count per image), grown until `seconds` of wall time are reached."""
+    import oracle
+    import synth
+    oracle.build()
+    cores = oracle.num_cores()
+    g, _ = synth.noisy_image(SEED * 10 + 1, H, W, SIGMAS[1])
+    rng = np.random.default_rng(0)
+    npix = max(cores * 2, 16)
+    total_solves = 0
+    t_total = 0.0
+    pix_done = em_done = 0
+    while t_total < seconds:
+        pix = rng.choice(H * W, npix, replace=False)
+        t0 = time.perf_counter()
+        oracle.nlem(g, K_PATCH, S_WIN, 10 * SIGMAS[1], RHO, CAP, tol=TOL, check_every=CHECK, pixels=pix)
+        probs = rng.choice(EM_B, max(npix // 3, 1), replace=False)
+        pts = synth.em_points(SEED, probs, EM_N, EM_D)
+        w = synth.em_weights(SEED, probs, EM_N)
+        t1 = time.perf_counter()
+        oracle.em_admm_batch(pts, w, BOX[0], BOX[1], RHO, CAP, tol=TOL, check_every=CHECK)
+        t2 = time.perf_counter()
+        t_total += (t1 - t0) + (t2 - t1)
+        total_solves += npix + probs.size
+        pix_done += npix
+        em_done += probs.size
+        npix *= 2
+    return total_solves / t_total, cores, (f"{pix_done} NLEM pixels of the 512x512 sigma=20 image and {em_done} "
+                                           f"standalone 441x49 problems, rho=1, tol 1e-4 every 10, cap 300, "
+                                           f"{t_total:.1f} s of wall time on {cores} threads")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rate, cores, sample = cpu_sample_rate(max(args.cpu_seconds, 5.0) * max(args.steps, 1) / 5.0)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "NLEM 3x512x512 (sigma 10/20/40, k=7, S=21) + em_solve 262144x441x49, rho=1, "
+                                   "tol 1e-4 cap 300", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1501_03879_gb300 as nl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = nl.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- inputs (each rank its own images and batch: weak scaling) ----
+    imgs_h, imgs = [], []
+    for i, sg in enumerate(SIGMAS):
+        g, _ = synth.noisy_image(SEED * 10 + i + 100 * rank, H, W, sg)
+        imgs_h.append(g)
+        imgs.append(torch.from_numpy(g).to(dev))
+    B = args.em_batch
+    pts = torch.empty((B, EM_N, EM_D), dtype=torch.float32, device=dev)
+    if not os.path.exists(synth.SYNTH_LIB):
+        synth.build_device_generator()
+    synth.device_em_points(SEED + rank, B, EM_N, EM_D, pts.data_ptr(), stream.cuda_stream)
+    wts = torch.from_numpy(synth.em_weights(SEED + rank, np.arange(B), EM_N)).to(dev)
+    outs = [dict(out=torch.empty((H, W), device=dev), iters_used=torch.empty((H, W), dtype=torch.int32, device=dev),
+                 residual=torch.empty((H, W), device=dev)) for _ in SIGMAS]
+    em_out = dict(x=torch.empty((B, EM_D), device=dev), iters_used=torch.empty(B, dtype=torch.int32, device=dev),
+                  residual=torch.empty(B, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        for i, sg in enumerate(SIGMAS):
+            if ev is not None:
+                ev["nlem"][i][0].record(stream)
+            nl.nlem_denoise(imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=RHO, iters=CAP, box=BOX, tol=TOL,
+                            check_every=CHECK, ctx=ctx, out=outs[i])
+            if ev is not None:
+                ev["nlem"][i][1].record(stream)
+        if ev is not None:
+            ev["em"][0].record(stream)
+        nl.em_solve_batch(pts, wts, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK, ctx=ctx, out=em_out)
+        if ev is not None:
+            ev["em"][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step and per-kernel CUDA events, L2 flushed in between ----
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    events = [dict(step=(mk(), mk()), nlem=[(mk(), mk()) for _ in SIGMAS], em=(mk(), mk())) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        events[k]["step"][0].record(stream)
+        step(events[k])
+        events[k]["step"][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e["step"][0].elapsed_time(e["step"][1]) for e in events]
+    nlem_ms = [sum(a.elapsed_time(b) for a, b in e["nlem"]) for e in events]
+    em_ms = [e["em"][0].elapsed_time(e["em"][1]) for e in events]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    solves_per_step = len(SIGMAS) * H * W + B
+    value = solves_per_step * args.steps * world / t_total
+    mpix = len(SIGMAS) * H * W * args.steps / (sum(nlem_ms) / 1e3) / 1e6
+    em_rate = B * args.steps / (sum(em_ms) / 1e3)
+
+    # ---- algorithmic work of the last timed step (iteration counts from the outputs) ----
+    n_map = window_counts(H, W, S_WIN)
+    nlem_fl = sum(nlem_flops(n_map, o["iters_used"].cpu().numpy().astype(np.float64), EM_D) for o in outs)
+    em_iters = em_out["iters_used"].cpu().numpy()
+    em_fl = em_flops(em_iters, EM_N, EM_D)
+    nlem_iters = np.concatenate([o["iters_used"].cpu().numpy().reshape(-1) for o in outs])
+    tf_chain, sms = nl.nlem_fp32_peak(ctx)
+    sm_mhz_max = clk.get("sm_max_mhz") or 2070.0
+    peak_alu = sms * 128 * 2 * sm_mhz_max * 1e6 / 1e12          # FP32 lanes x FMA x clock
+    nlem_avg_ms = statistics.mean(nlem_ms) / len(SIGMAS)
+    em_avg_ms = statistics.mean(em_ms)
+    nlem_ach = nlem_fl / len(SIGMAS) / (nlem_avg_ms / 1e3) / 1e12
+    em_ach = em_fl / (em_avg_ms / 1e3) / 1e12
+    dominant = "nlem_kernel" if sum(nlem_ms) >= sum(em_ms) else "em_batch_kernel"
+    ach = nlem_ach if dominant == "nlem_kernel" else em_ach
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": ach / peak_alu, "traffic": None,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz_max:.0f} MHz",
+                "fma_chain_measured_tflops": tf_chain,
+                "per_kernel": {"nlem_kernel": {"tflops": nlem_ach, "frac": nlem_ach / peak_alu,
+                                               "avg_ms": nlem_avg_ms},
+                               "em_batch_kernel": {"tflops": em_ach, "frac": em_ach / peak_alu,
+                                                   "avg_ms": em_avg_ms}}}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host_imgs = [torch.from_numpy(g).pin_memory() for g in imgs_h]
+        host_out = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in SIGMAS]
+        host_pts = torch.empty((B, EM_N, EM_D), dtype=torch.float32).pin_memory()
+        host_pts.copy_(pts)
+        host_w = wts.cpu().pin_memory()
+        host_x = torch.empty((B, EM_D), dtype=torch.float32).pin_memory()
+        dpts = pts          # device buffers reused; the host copy is the input
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            for i, sg in enumerate(SIGMAS):
+                nl.nlem_denoise_host(host_imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=RHO, iters=CAP,
+                                     box=BOX, tol=TOL, check_every=CHECK, ctx=ctx, out=host_out[i], device=local)
+            dpts.copy_(host_pts, non_blocking=True)
+            wts.copy_(host_w, non_blocking=True)
+            nl.em_solve_batch(dpts, wts, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK, ctx=ctx,
+                              out=em_out)
+            host_x.copy_(em_out["x"], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        h2d = len(SIGMAS) * H * W * 4 + B * EM_N * EM_D * 4 + B * EM_N * 4
+        d2h = len(SIGMAS) * H * W * 4 + B * EM_D * 4
+        e2e = {"value": solves_per_step * args.steps * world / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        del host_pts
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample = cpu_sample_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "configuration 2: NLEM 3x512x512 (sigma 10/20/40, 7x7 patches, 21x21 window, "
+                                   "h=10 sigma) + em_solve 262144 problems n=441 d=49; rho=1, tol 1e-4 every 10, "
+                                   "cap 300", "em_batch": B, "l2": "flushed between timed steps (512 MB write)"},
+            "mpixel_per_s": mpix, "em_batch_solves_per_s": em_rate,
+            "iterations": {"nlem_mean": float(nlem_iters.mean()), "nlem_cap_hit": float(np.mean(nlem_iters >= CAP)),
+                           "em_mean": float(em_iters.mean()), "em_cap_hit": float(np.mean(em_iters >= CAP))},
+            "roofline": roofline, "clocks": clk, "gpu_launches": 4 * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

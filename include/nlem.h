@@ -1,0 +1,147 @@
+/*
+ * nlem.h - C ABI of libnlem.so: constrained Euclidean medians by EM-ADMM and Non-Local
+ * Euclidean Medians (NLEM) denoising on NVIDIA GB300 (sm_103a).
+ *
+ * Method: K. N. Chaudhury and K. R. Ramakrishnan, "A new ADMM algorithm for the Euclidean
+ * median and its application to robust patch regression", arXiv 1501.03879.
+ *
+ * Conventions shared by every call
+ *   - Return value: 0 = OK, > 0 = warning, < 0 = error (NLEM_ERR_*).  On error no work has
+ *     been queued; nlem_last_error() returns a message (thread-local).
+ *   - Array arguments are caller-owned DEVICE pointers unless the name ends in _host.  The
+ *     library never frees or retains them beyond the call's stream work.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream); outputs are valid once that stream has reached the call's work.
+ *   - The library owns only what lives inside an nlem_ctx (workspace, tuning cache, graphs).
+ *   - No C++ exception crosses this boundary.  Every entry point is thread-compatible: use
+ *     one nlem_ctx per host thread.
+ */
+#ifndef NLEM_H_
+#define NLEM_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NLEM_OK 0
+#define NLEM_WARN_NOT_CONVERGED 1   /* reserved: per-problem convergence is in iters_used */
+#define NLEM_ERR_INVALID (-1)       /* an argument is out of range */
+#define NLEM_ERR_CUDA (-2)          /* a CUDA call failed (message says which) */
+#define NLEM_ERR_OOM (-3)           /* workspace allocation failed */
+#define NLEM_ERR_TIMEOUT (-4)       /* a bounded device wait ran out */
+#define NLEM_ERR_UNSUPPORTED (-5)   /* size outside what the kernels handle */
+
+#define NLEM_PREC_FP32 0            /* patch distances in FP32 on CUDA cores */
+#define NLEM_PREC_BF16 1            /* cross terms <P_i,P_j> in BF16 on tensor cores, FP32 accumulate */
+
+#define NLEM_INIT_WEIGHTED_MEAN 0   /* z0 = P_C(sum w_j P_j / sum w_j): the NLM patch (Sec. 3) */
+#define NLEM_INIT_NOISY_PATCH 1     /* z0 = P_C(P_i): the noisy patch (Sec. 3) */
+
+typedef struct nlem_ctx nlem_ctx;
+
+/* C = [lo, hi]^d, the box of Sec. 3 (e.g. [0, 255] for 8-bit grayscale). */
+typedef struct {
+  float lo, hi;
+} nlem_box;
+
+/* Options shared by the solver entry points.  Fill with nlem_options_default(). */
+typedef struct {
+  float tol;          /* > 0: stop when both relative residuals < tol (checked every
+                         check_every iterations and at the cap); <= 0: run exactly `iters` */
+  int check_every;    /* residual check period m >= 1 */
+  int precision;      /* NLEM_PREC_FP32 or NLEM_PREC_BF16 (nlem_denoise only) */
+  int init;           /* NLEM_INIT_* (nlem_denoise only; em_solve_batch uses x0) */
+  int fp64_check;     /* != 0: also compute, in FP64 on the GPU, the objective of problem (1)
+                         and its optimality residual at the returned point (see outputs) */
+  int reserved[3];
+} nlem_options;
+
+void nlem_options_default(nlem_options* opt);
+
+/* Last error message of the calling thread ("" if none). */
+const char* nlem_last_error(void);
+
+/* Library version string. */
+const char* nlem_version(void);
+
+/* Create / destroy a context bound to CUDA device `device`.  The context owns the
+ * workspace, the tile-shape tuning cache and captured CUDA graphs. */
+int nlem_ctx_create(nlem_ctx** ctx, int device);
+int nlem_ctx_destroy(nlem_ctx* ctx);
+
+/*
+ * em_solve - one constrained Euclidean median, problem (1) of Sec. 1:
+ *     z* ~ argmin_{z in C} sum_k w_k ||z - a_k||_2,  C = [box.lo, box.hi]^d,
+ * by Algorithm 1 (EM-ADMM, Sec. 2) with penalty mu = rho, y_k = 0 and z started at
+ * P_C(weighted mean), run for exactly `iters` iterations.
+ *   points  [n][d] float32, row-major (device)      weights [n] float32 >= 0 (device)
+ *   x_out   [d] float32 (device)
+ * Errors: -1 if n < 1, d < 1 or d > 128, rho <= 0 or not finite, iters < 0, lo > hi or not
+ * finite.  Points or weights that are not finite, or negative weights, give x_out = NaN.
+ * iters == 0 returns P_C(weighted mean).
+ */
+int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, int d,
+             nlem_box box, float rho, int iters, float* x_out, void* stream);
+
+/*
+ * em_solve_batch - B independent problems of the same (n, d), Algorithm 1 on each.
+ *   points   [B][n][d] float32 (device)     weights [B][n] float32 (device)
+ *   x0       [B][d] float32 start points (device) or NULL for P_C(weighted mean)
+ *   opt      options (NULL = defaults: fixed iteration count)
+ *   x_out    [B][d] float32 (device)
+ *   iters_used [B] int32 or NULL: iterations run (-1 marks a problem with non-finite
+ *            input or a negative weight; its x_out is NaN)
+ *   residual [B] float32 or NULL: max(r_pri, r_dual) at the last check, where
+ *            r_pri  = sqrt(sum_k ||x_k - z||^2) / max(sqrt(sum_k ||x_k||^2), sqrt(n)||z||)
+ *            r_dual = sqrt(n) ||z - z_prev|| / sqrt(sum_k ||y_k / rho||^2)
+ *            (scaled-form ADMM residuals of Boyd et al. 2011, as cited in Sec. 2)
+ *   obj64 / kkt64 [B] double or NULL (only with opt->fp64_check): F(z) of problem (1) and
+ *            the projected-gradient optimality residual ||z - P_C(z - g/sum w)||, both in FP64.
+ * Errors as em_solve; -5 if n exceeds the largest problem the on-chip kernels hold for this
+ * d and no workspace could be created for the streaming kernel.
+ */
+int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n,
+                   int d, nlem_box box, float rho, int iters, const float* x0,
+                   const nlem_options* opt, float* x_out, int* iters_used, float* residual,
+                   double* obj64, double* kkt64, void* stream);
+
+/*
+ * nlem_denoise - NLEM of Sec. 3 (Eq. L1regression) on one grayscale image.
+ * For every pixel i: P_j = the patch x patch window of the image centred at j
+ * (reflect-padded at the border, no edge repeat), S(i) = centres j of the window x window
+ * search window around i that lie in the image (clipped at the border, so n varies),
+ * w_ij = exp(-||P_i - P_j||^2 / h^2) (not divided by patch^2; w_ii = 1), then EM-ADMM over
+ * C = [box.lo, box.hi]^(patch^2) with mu = rho, and out[i] = centre coordinate of the solution.
+ *   image [H][pitch] float32 (device), pitch >= W elements
+ *   out   [H][W] float32 (device)
+ *   iters_used [H][W] int32 or NULL;  residual [H][W] float32 or NULL (as em_solve_batch)
+ *   obj64 / kkt64 [H][W] double or NULL (opt->fp64_check)
+ * Errors: -1 if patch or window is even or < 1, patch > min(H, W),
+ * h <= 0, rho <= 0, iters < 0, lo > hi; -5 if patch*patch > 128 or the window holds more
+ * points than the kernels support (window <= 31).
+ */
+int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch,
+                 int window, float h, float rho, int iters, nlem_box box,
+                 const nlem_options* opt, float* out, int* iters_used, float* residual,
+                 double* obj64, double* kkt64, void* stream);
+
+/*
+ * nlem_denoise_host - nlem_denoise on HOST buffers: copies image_host [H][W] to the device,
+ * denoises, copies out_host [H][W] back, and waits for completion.  Uses context workspace.
+ * Host buffers may be pageable or pinned (pinned is faster).
+ */
+int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int patch, int window,
+                      float h, float rho, int iters, nlem_box box, const nlem_options* opt,
+                      float* out_host, int* iters_used_host, void* stream);
+
+/*
+ * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an
+ * FMA as 2 flops), from a register-only FMA-chain kernel timed with CUDA events; also
+ * returns the SM count.  Used as the roofline denominator of the ALU-bound kernels.
+ */
+int nlem_fp32_peak(nlem_ctx* ctx, double* tflops, int* sm_count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLEM_H_ */

@@ -1,0 +1,28 @@
+"""GB300-native constrained Euclidean medians (EM-ADMM) and NLEM denoising.
+
+Thin Python binding over libnlem.so (C ABI in include/nlem.h).  Every step of the
+computation runs in the library's CUDA kernels; this module only marshals arguments
+(torch CUDA tensors -> device pointers, the current CUDA stream) and raises on errors.
+There is no CPU fallback: importing the binding fails loudly if the library is missing.
+
+Method: Chaudhury & Ramakrishnan, "A new ADMM algorithm for the Euclidean median and its
+application to robust patch regression" (arXiv 1501.03879): problem (1), Algorithm 1
+(EM-ADMM) and NLEM (Sec. 3).
+"""
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    INIT_NOISY_PATCH,
+    INIT_WEIGHTED_MEAN,
+    PREC_BF16,
+    PREC_FP32,
+    Context,
+    NlemError,
+    em_solve,
+    em_solve_batch,
+    lib_path,
+    load_library,
+    nlem_denoise,
+    nlem_denoise_host,
+    nlem_fp32_peak,
+)

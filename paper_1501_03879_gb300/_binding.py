@@ -1,0 +1,269 @@
+"""ctypes binding of libnlem.so.  Argument marshalling only; names follow include/nlem.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(PKG, "lib", "libnlem.so")
+
+PREC_FP32 = 0
+PREC_BF16 = 1
+INIT_WEIGHTED_MEAN = 0
+INIT_NOISY_PATCH = 1
+
+_ERRNAMES = {-1: "NLEM_ERR_INVALID", -2: "NLEM_ERR_CUDA", -3: "NLEM_ERR_OOM", -4: "NLEM_ERR_TIMEOUT",
+             -5: "NLEM_ERR_UNSUPPORTED"}
+
+
+class NlemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
+                ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libnlem.so (built in-tree by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libnlem.so not found at {_LIB_PATH}; build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i, ll, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float
+        lib.nlem_last_error.restype = ctypes.c_char_p
+        lib.nlem_version.restype = ctypes.c_char_p
+        lib.nlem_options_default.argtypes = [ctypes.POINTER(_Options)]
+        lib.nlem_ctx_create.argtypes = [ctypes.POINTER(vp), i]
+        lib.nlem_ctx_destroy.argtypes = [vp]
+        lib.em_solve.argtypes = [vp, vp, vp, i, i, _Box, f, i, vp, vp]
+        lib.em_solve_batch.argtypes = [vp, vp, vp, ll, i, i, _Box, f, i, vp, ctypes.POINTER(_Options), vp, vp, vp,
+                                       vp, vp, vp]
+        lib.nlem_denoise.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp, vp,
+                                     vp, vp]
+        lib.nlem_denoise_host.argtypes = [vp, vp, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
+                     "nlem_denoise_host", "nlem_fp32_peak"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise NlemError(rc, load_library().nlem_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("device tensor required (use nlem_denoise_host for host buffers)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    import torch
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _stream(device):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False):
+    o = _Options()
+    load_library().nlem_options_default(ctypes.byref(o))
+    o.tol = float(tol)
+    o.check_every = int(check_every)
+    o.precision = int(precision)
+    o.init = int(init)
+    o.fp64_check = 1 if fp64_check else 0
+    return o
+
+
+class Context:
+    """Owns an nlem_ctx (workspace, tuning cache) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.nlem_ctx_create(ctypes.byref(h), int(device)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            load_library().nlem_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ctxs: dict[int, Context] = {}
+
+
+def _ctx(device) -> Context:
+    import torch
+    dev = torch.device(device).index if device is not None else torch.cuda.current_device()
+    if dev is None:
+        dev = torch.cuda.current_device()
+    c = _ctxs.get(dev)
+    if c is None:
+        c = _ctxs[dev] = Context(dev)
+    return c
+
+
+def em_solve(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, out=None, ctx: Context | None = None):
+    """Problem (1) for one point set: points [n, d] float32 CUDA, weights [n]; returns x [d]."""
+    import torch
+    n, d = points.shape
+    _need(points, torch.float32, (n, d), "points")
+    _need(weights, torch.float32, (n,), "weights")
+    c = ctx or _ctx(points.device)
+    if out is None:
+        out = torch.empty(d, dtype=torch.float32, device=points.device)
+    _check(load_library().em_solve(c.handle, _ptr(points), _ptr(weights), n, d, _Box(*box), float(rho), int(iters),
+                                   _ptr(out), _stream(points.device)))
+    return out
+
+
+def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
+                   fp64_check=False, ctx: Context | None = None, out=None):
+    """Algorithm 1 on B problems: points [B, n, d], weights [B, n] (float32 CUDA).
+    Returns dict(x [B,d], iters_used [B] int32, residual [B], obj64/kkt64 [B] float64 if fp64_check)."""
+    import torch
+    B, n, d = points.shape
+    _need(points, torch.float32, (B, n, d), "points")
+    _need(weights, torch.float32, (B, n), "weights")
+    if x0 is not None:
+        _need(x0, torch.float32, (B, d), "x0")
+    c = ctx or _ctx(points.device)
+    dev = points.device
+    res = out or {}
+    x = res.get("x")
+    if x is None:
+        x = torch.empty((B, d), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty(B, dtype=torch.int32, device=dev)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.empty(B, dtype=torch.float32, device=dev)
+    obj = kkt = None
+    if fp64_check:
+        obj = torch.empty(B, dtype=torch.float64, device=dev)
+        kkt = torch.empty(B, dtype=torch.float64, device=dev)
+    o = _options(tol, check_every, fp64_check=fp64_check)
+    _check(load_library().em_solve_batch(c.handle, _ptr(points), _ptr(weights), B, n, d, _Box(*box), float(rho),
+                                         int(iters), _ptr(x0), ctypes.byref(o), _ptr(x), _ptr(used), _ptr(resid),
+                                         _ptr(obj), _ptr(kkt), _stream(dev)))
+    r = dict(x=x, iters_used=used, residual=resid)
+    if fp64_check:
+        r.update(obj64=obj, kkt64=kkt)
+    return r
+
+
+def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
+                 precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None,
+                 out=None):
+    """NLEM (Sec. 3) of a float32 CUDA image [H, W].  Returns dict(out [H,W], iters_used,
+    residual[, obj64, kkt64])."""
+    import torch
+    H, W = image.shape
+    _need(image, torch.float32, (H, W), "image")
+    c = ctx or _ctx(image.device)
+    dev = image.device
+    res = out or {}
+    o_img = res.get("out")
+    if o_img is None:
+        o_img = torch.empty((H, W), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty((H, W), dtype=torch.int32, device=dev)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.empty((H, W), dtype=torch.float32, device=dev)
+    obj = kkt = None
+    if fp64_check:
+        obj = torch.empty((H, W), dtype=torch.float64, device=dev)
+        kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
+    o = _options(tol, check_every, precision, init, fp64_check)
+    _check(load_library().nlem_denoise(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h), float(rho),
+                                       int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
+                                       _ptr(obj), _ptr(kkt), _stream(dev)))
+    r = dict(out=o_img, iters_used=used, residual=resid)
+    if fp64_check:
+        r.update(obj64=obj, kkt64=kkt)
+    return r
+
+
+def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
+                      check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, ctx: Context | None = None,
+                      out=None, iters_used=None, device=0):
+    """NLEM on HOST buffers (numpy float32 [H, W] or CPU torch tensor, ideally pinned):
+    copies in, denoises and copies out inside the library.  Returns the host output."""
+    import numpy as np
+    import torch
+    if isinstance(image, np.ndarray):
+        img_t = torch.from_numpy(np.ascontiguousarray(image, dtype=np.float32))
+    else:
+        img_t = image.contiguous()
+    if img_t.is_cuda or img_t.dtype != torch.float32:
+        raise ValueError("host float32 image required")
+    H, W = img_t.shape
+    c = ctx or _ctx(torch.device("cuda", device))
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, pin_memory=img_t.is_pinned())
+    o = _options(tol, check_every, precision, init)
+    ip = ctypes.c_void_p(iters_used.data_ptr()) if iters_used is not None else None
+    _check(load_library().nlem_denoise_host(c.handle, ctypes.c_void_p(img_t.data_ptr()), H, W, int(patch),
+                                            int(window), float(h), float(rho), int(iters), _Box(*box),
+                                            ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), ip,
+                                            _stream(torch.device("cuda", c.device))))
+    return out
+
+
+def nlem_fp32_peak(ctx: Context | None = None):
+    """Measured FP32 FMA throughput (TFLOP/s) and SM count of the context's device."""
+    import torch
+    c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+    tf = ctypes.c_double()
+    sms = ctypes.c_int()
+    _check(load_library().nlem_fp32_peak(c.handle, ctypes.byref(tf), ctypes.byref(sms)))
+    return tf.value, sms.value

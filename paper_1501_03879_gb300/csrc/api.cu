@@ -1,0 +1,269 @@
+// C ABI of libnlem.so (declared in include/nlem.h): argument validation, context and
+// workspace ownership, dispatch to the kernels, and error reporting without exceptions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/nlem.h"
+#include "kernels.h"
+
+struct nlem_ctx {
+  int device = 0;
+  int sm_count = 0;
+  // workspace for the host-buffer entry point (grown on demand, freed by destroy)
+  float* ws_img = nullptr;
+  float* ws_out = nullptr;
+  int* ws_iters = nullptr;
+  size_t ws_pixels = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(NLEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite(float x) { return std::isfinite(x); }
+
+int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_options* opt) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  if (!(rho > 0.f) || !finite(rho)) return fail(NLEM_ERR_INVALID, "rho must be finite and > 0 (got %g)", rho);
+  if (iters < 0) return fail(NLEM_ERR_INVALID, "iters must be >= 0 (got %d)", iters);
+  if (!finite(box.lo) || !finite(box.hi) || box.lo > box.hi)
+    return fail(NLEM_ERR_INVALID, "box must satisfy lo <= hi, both finite (got [%g, %g])", box.lo, box.hi);
+  if (opt) {
+    if (opt->check_every < 1) return fail(NLEM_ERR_INVALID, "check_every must be >= 1");
+    if (!std::isfinite(opt->tol)) return fail(NLEM_ERR_INVALID, "tol must be finite");
+    if (opt->precision != NLEM_PREC_FP32 && opt->precision != NLEM_PREC_BF16)
+      return fail(NLEM_ERR_INVALID, "unknown precision %d", opt->precision);
+    if (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH)
+      return fail(NLEM_ERR_INVALID, "unknown init %d", opt->init);
+  }
+  return NLEM_OK;
+}
+
+nlemk::SolveParams make_params(nlem_box box, float rho, int iters, const nlem_options* opt, int d) {
+  nlemk::SolveParams p;
+  p.lo = box.lo;
+  p.hi = box.hi;
+  p.mu = rho;
+  p.inv_mu = 1.f / rho;
+  p.iters = iters;
+  p.tol = opt ? opt->tol : 0.f;
+  p.check_every = opt ? opt->check_every : 1;
+  p.d = d;
+  return p;
+}
+
+int set_device(nlem_ctx* ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return NLEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nlem_options_default(nlem_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->tol = 0.f;
+  opt->check_every = 1;
+  opt->precision = NLEM_PREC_FP32;
+  opt->init = NLEM_INIT_WEIGHTED_MEAN;
+  opt->fp64_check = 0;
+}
+
+const char* nlem_last_error(void) { return g_err.c_str(); }
+
+const char* nlem_version(void) { return "nlem-gb300 0.1 (sm_103a)"; }
+
+int nlem_ctx_create(nlem_ctx** ctx, int device) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx out-pointer is NULL");
+  *ctx = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(NLEM_ERR_INVALID, "device %d out of range (%d devices)", device, count);
+  nlem_ctx* c = new (std::nothrow) nlem_ctx();
+  if (!c) return fail(NLEM_ERR_OOM, "out of host memory");
+  c->device = device;
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute(MultiProcessorCount)");
+  }
+  *ctx = c;
+  return NLEM_OK;
+}
+
+int nlem_ctx_destroy(nlem_ctx* ctx) {
+  if (!ctx) return NLEM_OK;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->ws_img);
+  cudaFree(ctx->ws_out);
+  cudaFree(ctx->ws_iters);
+  delete ctx;
+  return NLEM_OK;
+}
+
+int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n, int d,
+                   nlem_box box, float rho, int iters, const float* x0, const nlem_options* opt,
+                   float* x_out, int* iters_used, float* residual, double* obj64, double* kkt64,
+                   void* stream) {
+  int rc = check_common(ctx, box, rho, iters, opt);
+  if (rc) return rc;
+  if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
+  if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
+  if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
+  if (!points || !weights || !x_out) return fail(NLEM_ERR_INVALID, "points, weights and x_out must be non-NULL");
+  if (B == 0) return NLEM_OK;
+  if (d > 120 || n > nlemk::em_capacity(d))
+    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d, d <= 120)", n,
+                d, nlemk::em_capacity(d));
+  if ((rc = set_device(ctx))) return rc;
+  nlemk::EmLaunch L;
+  L.pts = points;
+  L.w = weights;
+  L.B = B;
+  L.n = n;
+  L.d = d;
+  L.prm = make_params(box, rho, iters, opt, d);
+  L.x0 = x0;
+  L.x_out = x_out;
+  L.iters_used = iters_used;
+  L.resid = residual;
+  const bool chk = opt && opt->fp64_check;
+  L.obj64 = chk ? obj64 : nullptr;
+  L.kkt64 = chk ? kkt64 : nullptr;
+  L.sm_count = ctx->sm_count;
+  L.stream = (cudaStream_t)stream;
+  int e = nlemk::launch_em_batch(L);
+  if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for n = %d, d = %d", n, d);
+  if (e != 0) return cuda_fail((cudaError_t)e, "em_solve_batch launch");
+  return NLEM_OK;
+}
+
+int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, int d, nlem_box box, float rho,
+             int iters, float* x_out, void* stream) {
+  return em_solve_batch(ctx, points, weights, 1, n, d, box, rho, iters, nullptr, nullptr, x_out, nullptr, nullptr,
+                        nullptr, nullptr, stream);
+}
+
+int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                 float rho, int iters, nlem_box box, const nlem_options* opt, float* out, int* iters_used,
+                 float* residual, double* obj64, double* kkt64, void* stream) {
+  int rc = check_common(ctx, box, rho, iters, opt);
+  if (rc) return rc;
+  if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1 (got %dx%d)", H, W);
+  if (pitch < W) return fail(NLEM_ERR_INVALID, "pitch %d < W %d", pitch, W);
+  if (patch < 1 || (patch % 2) == 0) return fail(NLEM_ERR_INVALID, "patch must be odd and >= 1 (got %d)", patch);
+  if (window < 1 || (window % 2) == 0) return fail(NLEM_ERR_INVALID, "window must be odd and >= 1 (got %d)", window);
+  int side = H < W ? H : W;
+  if (patch > side) return fail(NLEM_ERR_INVALID, "patch %d exceeds the image side %d", patch, side);
+  if (!(h > 0.f) || !finite(h)) return fail(NLEM_ERR_INVALID, "h must be finite and > 0 (got %g)", h);
+  if (!image || !out) return fail(NLEM_ERR_INVALID, "image and out must be non-NULL");
+  if (opt && opt->precision == NLEM_PREC_BF16)
+    return fail(NLEM_ERR_UNSUPPORTED, "BF16 cross-term weights are not built into this library");
+  if (patch * patch > 128) return fail(NLEM_ERR_UNSUPPORTED, "patch^2 must be <= 128");
+  int cap = nlemk::nlem_capacity(patch);
+  if (cap == 0) return fail(NLEM_ERR_UNSUPPORTED, "patch %d not compiled (5, 7, 9 are)", patch);
+  if (window * window > cap)
+    return fail(NLEM_ERR_UNSUPPORTED, "window %d holds %d points; the patch-%d kernels hold %d", window,
+                window * window, patch, cap);
+  if ((rc = set_device(ctx))) return rc;
+  nlemk::NlemLaunch L;
+  L.img = image;
+  L.H = H;
+  L.W = W;
+  L.pitch = pitch;
+  L.patch = patch;
+  L.S = window;
+  L.inv_h2 = 1.f / (h * h);
+  L.inv_h2_exact = 1.0 / ((double)h * (double)h);
+  L.prm = make_params(box, rho, iters, opt, patch * patch);
+  L.init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
+  L.out = out;
+  L.iters_used = iters_used;
+  L.resid = residual;
+  const bool chk = opt && opt->fp64_check;
+  L.obj64 = chk ? obj64 : nullptr;
+  L.kkt64 = chk ? kkt64 : nullptr;
+  L.sm_count = ctx->sm_count;
+  L.stream = (cudaStream_t)stream;
+  int e = nlemk::launch_nlem_fp32(L);
+  if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for patch %d, window %d", patch, window);
+  if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise launch");
+  return NLEM_OK;
+}
+
+int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int patch, int window, float h,
+                      float rho, int iters, nlem_box box, const nlem_options* opt, float* out_host,
+                      int* iters_used_host, void* stream) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  if (!image_host || !out_host) return fail(NLEM_ERR_INVALID, "image_host and out_host must be non-NULL");
+  if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  size_t npix = (size_t)H * W;
+  if (npix > ctx->ws_pixels) {
+    cudaFree(ctx->ws_img);
+    cudaFree(ctx->ws_out);
+    cudaFree(ctx->ws_iters);
+    ctx->ws_img = ctx->ws_out = nullptr;
+    ctx->ws_iters = nullptr;
+    ctx->ws_pixels = 0;
+    if (cudaMalloc(&ctx->ws_img, npix * 4) != cudaSuccess || cudaMalloc(&ctx->ws_out, npix * 4) != cudaSuccess ||
+        cudaMalloc(&ctx->ws_iters, npix * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(NLEM_ERR_OOM, "workspace of %zu pixels could not be allocated", npix);
+    }
+    ctx->ws_pixels = npix;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->ws_img, image_host, npix * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy image to device");
+  rc = nlem_denoise(ctx, ctx->ws_img, H, W, W, patch, window, h, rho, iters, box, opt, ctx->ws_out,
+                    iters_used_host ? ctx->ws_iters : nullptr, nullptr, nullptr, nullptr, stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out_host, ctx->ws_out, npix * 4, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy result to host");
+  if (iters_used_host) {
+    e = cudaMemcpyAsync(iters_used_host, ctx->ws_iters, npix * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy iteration counts to host");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "nlem_denoise_host");
+  return NLEM_OK;
+}
+
+int nlem_fp32_peak(nlem_ctx* ctx, double* tflops, int* sm_count) {
+  if (!ctx || !tflops) return fail(NLEM_ERR_INVALID, "ctx and tflops must be non-NULL");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  int e = nlemk::measure_fp32_peak(ctx->sm_count, tflops);
+  if (e != 0) return cuda_fail((cudaError_t)e, "fp32 peak probe");
+  if (sm_count) *sm_count = ctx->sm_count;
+  return NLEM_OK;
+}
+
+}  // extern "C"

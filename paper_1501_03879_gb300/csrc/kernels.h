@@ -1,0 +1,50 @@
+// Internal launch descriptors shared by the C-ABI layer and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "admm_core.cuh"
+
+namespace nlemk {
+
+struct EmLaunch {
+  const float* pts;
+  const float* w;
+  long long B;
+  int n, d;
+  SolveParams prm;
+  const float* x0;
+  float* x_out;
+  int* iters_used;
+  float* resid;
+  double* obj64;
+  double* kkt64;
+  int sm_count;
+  cudaStream_t stream;
+};
+
+struct NlemLaunch {
+  const float* img;
+  int H, W, pitch, patch, S;
+  float inv_h2;
+  double inv_h2_exact;   // 1/h^2 in double, for the FP64 check
+  SolveParams prm;
+  int init_mode;
+  float* out;
+  int* iters_used;
+  float* resid;
+  double* obj64;
+  double* kkt64;
+  int sm_count;
+  cudaStream_t stream;
+};
+
+// Return cudaError_t codes (0 = launched), or -1 when no compiled shape holds the problem.
+int launch_em_batch(const EmLaunch& L);
+int launch_nlem_fp32(const NlemLaunch& L);
+int em_capacity(int d);
+int nlem_capacity(int patch);
+
+// FP32 FMA-chain throughput probe; returns cudaError_t.
+int measure_fp32_peak(int sm_count, double* tflops);
+
+}  // namespace nlemk

@@ -1,0 +1,267 @@
+// EM-ADMM kernel templates: standalone batches of Euclidean-median problems (problem (1), Sec. 1) and
+// fused NLEM denoising (Sec. 3, Eq. L1regression).  One CTA solves one problem at a time
+// with the register-resident solver of admm_core.cuh and loops over problems.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "admm_core.cuh"
+#include "kernels.h"
+
+namespace nlemk {
+
+// ------------------------------------------------------------------------------------------
+// standalone batch: points [B][n][d] and weights [B][n] streamed from HBM into the CTA's
+// shared-memory point rows, one problem per CTA iteration
+// ------------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
+em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, long long B, int n,
+                int d, SolveParams prm, const float* __restrict__ x0, float* __restrict__ x_out,
+                int* __restrict__ iters_used, float* __restrict__ resid, double* __restrict__ obj64,
+                double* __restrict__ kkt64) {
+  extern __shared__ float4 smem_raw[];
+  Smem<C> sm(reinterpret_cast<float*>(smem_raw));
+  const int t = threadIdx.x;
+  const int dd = C::D > 0 ? C::D : d;
+  for (long long b = blockIdx.x; b < B; b += gridDim.x) {
+    const float* P = pts_g + (size_t)b * n * dd;
+    const float* Wt = w_g + (size_t)b * n;
+    // points -> [j][slice][QA] rows; inactive rows and (for runtime d) phantom slots zero
+    int bad = 0;
+    if (C::D == 0) {
+      for (int i = t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
+      __syncthreads();
+    } else {
+      for (int i = n * C::DP + t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
+    }
+    for (int idx = t; idx < n * dd; idx += C::NT) {
+      const int j = idx / dd, q = idx - j * dd;
+      const int sg = q / C::Q, i = q - sg * C::Q;
+      const float v = __ldg(P + idx);
+      bad |= !isfinite(v);
+      sm.pts[j * C::DP + sg * C::QA + i] = v;
+    }
+    for (int j = t; j < C::CAP; j += C::NT) {
+      float lam = 0.f;
+      if (j < n) {
+        const float w = __ldg(Wt + j);
+        bad |= !(w >= 0.f) || !isfinite(w);
+        lam = w * prm.inv_mu;
+      }
+      sm.lam[j] = lam;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+      for (int q = t; q < dd; q += C::NT) x_out[(size_t)b * dd + q] = __int_as_float(0x7fc00000);
+      if (t == 0) {
+        if (iters_used) iters_used[b] = -1;
+        if (resid) resid[b] = __int_as_float(0x7fc00000);
+        if (obj64) obj64[b] = __longlong_as_double(0x7ff8000000000000ll);
+        if (kkt64) kkt64[b] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      __syncthreads();
+      continue;
+    }
+    if (x0) {
+      for (int i = t; i < C::VEC; i += C::NT) {
+        const int sg = i / C::QA, slot = i - sg * C::QA;
+        const int real = slice_real<C>(sg, dd);
+        const float z = slot < real ? clampf(__ldg(x0 + (size_t)b * dd + sg * C::Q + slot), prm.lo, prm.hi) : 0.f;
+        sm.zv[i] = z;
+        sm.cv[i] = z;
+        sm.sgv[i] = 0.f;
+      }
+      __syncthreads();
+    } else {
+      float wreg[C::P];
+      const int pg = lane_group<C>();
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) {
+        const int j = pg + p * C::NG;
+        wreg[p] = j < n ? __ldg(Wt + j) : 0.f;
+      }
+      weighted_mean_start<C>(sm, wreg, n, dd, prm);
+    }
+    admm_iterate<C>(sm, n, dd, prm);
+    for (int q = t; q < dd; q += C::NT) {
+      const int sg = q / C::Q, i = q - sg * C::Q;
+      x_out[(size_t)b * dd + q] = sm.zv[sg * C::QA + i];
+    }
+    if (t == 0) {
+      if (iters_used) iters_used[b] = (int)sm.scal[2];
+      if (resid) resid[b] = sm.scal[3];
+    }
+    if (obj64 || kkt64) {
+      double F, R;
+      fp64_check<C>(sm, n, dd, prm, [&](int j) { return (double)__ldg(Wt + j); }, F, R);
+      if (t == 0) {
+        if (obj64) obj64[b] = F;
+        if (kkt64) kkt64[b] = R;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// NLEM: one pixel per CTA iteration.  Tile of the reflect-padded image around the clipped
+// search window -> patch rows in shared memory -> weights exp(-||P_i-P_j||^2/h^2) -> start
+// point -> EM-ADMM -> centre coordinate.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int reflect_idx(int x, int N) {
+  return x < 0 ? -x : (x >= N ? 2 * N - 2 - x : x);
+}
+
+template <class C, int K>
+__global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
+nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
+            SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
+            float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64) {
+  static_assert(K * K == C::D, "patch size must match the compiled dimension");
+  extern __shared__ float4 smem_raw[];
+  Smem<C> sm(reinterpret_cast<float*>(smem_raw));
+  const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
+  const bool last = (g == C::G - 1);
+  constexpr int HK = (K - 1) / 2;
+  const int R = (S - 1) / 2;
+  const long long npix = (long long)H * W;
+  for (long long pix = blockIdx.x; pix < npix; pix += gridDim.x) {
+    const int ir = (int)(pix / W), ic = (int)(pix - (long long)ir * W);
+    const int r0 = max(ir - R, 0), r1 = min(ir + R, H - 1);
+    const int c0 = max(ic - R, 0), c1 = min(ic + R, W - 1);
+    const int nwr = r1 - r0 + 1, nwc = c1 - c0 + 1, n = nwr * nwc;
+    const int TR = nwr + 2 * HK, TC = nwc + 2 * HK;
+    // tile rows r0-HK .. r1+HK, cols c0-HK .. c1+HK of the reflect-padded image
+    for (int i = t; i < TR * TC; i += C::NT) {
+      const int tr = i / TC, tc = i - tr * TC;
+      const int gr = reflect_idx(r0 - HK + tr, H), gc = reflect_idx(c0 - HK + tc, W);
+      sm.tile[i] = __ldg(img + (size_t)gr * pitch + gc);
+    }
+    for (int i = n * C::DP + t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
+    __syncthreads();
+    // patch rows: point j = window position (jr, jc) in row-major order, coordinate q = (qr, qc)
+    for (int idx = t; idx < n * C::D; idx += C::NT) {
+      const int j = idx / C::D, q = idx - j * C::D;
+      const int jr = j / nwc, jc = j - jr * nwc;
+      const int qr = q / K, qc = q - qr * K;
+      const int sg = q / C::Q, i = q - sg * C::Q;
+      sm.pts[j * C::DP + sg * C::QA + i] = sm.tile[(jr + qr) * TC + jc + qc];
+    }
+    // centre patch in slice layout (phantom slots zero)
+    for (int i = t; i < C::VEC; i += C::NT) {
+      const int sg = i / C::QA, slot = i - sg * C::QA;
+      float v = 0.f;
+      if (slot < slice_real<C>(sg, C::D)) {
+        const int q = sg * C::Q + slot;
+        const int qr = q / K, qc = q - qr * K;
+        v = sm.tile[(ir - r0 + qr) * TC + (ic - c0 + qc)];
+      }
+      sm.pcv[i] = v;
+    }
+    __syncthreads();
+    // weights (same lane layout as the solver)
+    float wreg[C::P];
+    {
+      float pc[C::Q];
+      load_slice<C>(sm.pcv + g * C::QA, last, pc);
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) {
+        const int j = pg + p * C::NG;
+        const float* arow = sm.pts + j * C::DP + g * C::QA;
+        float D0 = 0.f, D1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < C::NQA; ++i) {
+          const float4 a4 = load_quad<C>(arow, i, last);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int q = 4 * i + c;
+            if (q < C::Q) {
+              const float e = pc[q] - f4get(a4, c);
+              if (c & 1) D1 = fmaf(e, e, D1); else D0 = fmaf(e, e, D0);
+            }
+          }
+        }
+        const float Dp = point_sum<C>(D0 + D1);
+        const float w = j < n ? expf(-Dp * inv_h2) : 0.f;
+        wreg[p] = w;
+        if (g == 0) sm.lam[j] = w * prm.inv_mu;
+      }
+    }
+    if (init_mode == 1) {
+      for (int i = t; i < C::VEC; i += C::NT) {
+        const float z = clampf(sm.pcv[i], prm.lo, prm.hi);
+        const int sg = i / C::QA, slot = i - sg * C::QA;
+        const float zz = slot < slice_real<C>(sg, C::D) ? z : 0.f;
+        sm.zv[i] = zz;
+        sm.cv[i] = zz;
+        sm.sgv[i] = 0.f;
+      }
+      __syncthreads();
+    } else {
+      __syncthreads();   // lam visible, tile no longer needed (wred aliases it)
+      weighted_mean_start<C>(sm, wreg, n, C::D, prm);
+    }
+    admm_iterate<C>(sm, n, C::D, prm);
+    if (t == 0) {
+      constexpr int qc = (C::D - 1) / 2;
+      constexpr int sg = qc / C::Q, slot = qc - sg * C::Q;
+      out[pix] = sm.zv[sg * C::QA + slot];
+      if (iters_used) iters_used[pix] = (int)sm.scal[2];
+      if (resid) resid[pix] = sm.scal[3];
+    }
+    if (obj64 || kkt64) {
+      double F, Rk;
+      auto wfun = [&](int j) {
+        double D = 0.0;
+        for (int q = 0; q < C::D; ++q) {
+          const int sg = q / C::Q, i = q - sg * C::Q;
+          const double e = (double)sm.pcv[sg * C::QA + i] - (double)sm.pts[j * C::DP + sg * C::QA + i];
+          D += e * e;
+        }
+        return exp(-D * ih2);
+      };
+      fp64_check<C>(sm, n, C::D, prm, wfun, F, Rk);
+      if (t == 0) {
+        if (obj64) obj64[pix] = F;
+        if (kkt64) kkt64[pix] = Rk;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// dispatch tables
+// ------------------------------------------------------------------------------------------
+template <class C>
+inline int launch_em(const EmLaunch& L, int grid_mult) {
+  auto kern = em_batch_kernel<C>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+  if (e != cudaSuccess) return (int)e;
+  long long grid = L.B;
+  long long cap = (long long)L.sm_count * C::MIN_BLOCKS * grid_mult;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.pts, L.w, L.B, L.n, L.d, L.prm, L.x0, L.x_out,
+                                                          L.iters_used, L.resid, L.obj64, L.kkt64);
+  return (int)cudaGetLastError();
+}
+
+template <class C, int K>
+inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
+  if ((L.S + K - 1) * (L.S + K - 1) > C::SZ_WRED) return -1;   // tile must fit its region
+  auto kern = nlem_kernel<C, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+  if (e != cudaSuccess) return (int)e;
+  long long npix = (long long)L.H * L.W;
+  long long grid = npix;
+  long long cap = (long long)L.sm_count * C::MIN_BLOCKS * grid_mult;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.img, L.H, L.W, L.pitch, L.S, L.inv_h2, L.inv_h2_exact, L.prm,
+                                                          L.init_mode, L.out, L.iters_used, L.resid, L.obj64,
+                                                          L.kkt64);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace nlemk
