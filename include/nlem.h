@@ -134,6 +134,38 @@ int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int 
                       float h, float rho, int iters, nlem_box box, const nlem_options* opt,
                       float* out_host, int* iters_used_host, void* stream);
 
+/* One image of a batch.  The struct itself is host memory; its pointers are device pointers. */
+typedef struct {
+  const float* image;   /* [H][pitch] float32 */
+  float* out;           /* [H][W] float32 */
+  int* iters_used;      /* [H][W] int32 or NULL */
+  float* residual;      /* [H][W] float32 or NULL */
+  int H, W, pitch;
+  int patch, window;    /* odd; patch 5 or 7 in the batched kernel; window^2 <= 441 */
+  float h;              /* weight scale, e.g. 10 * sigma */
+} nlem_image_desc;
+
+/*
+ * nlem_denoise_batch - NLEM (as nlem_denoise) on `count` images of uneven sizes, patch and
+ * window sizes in ONE persistent kernel launch: every (image, pixel) pair is a work item that
+ * CTAs take from a device work queue in the context workspace.  The queue reset and the launch
+ * are captured once in a CUDA graph per distinct batch (same descriptors and parameters) and
+ * replayed on later calls.  The launch shape (kernel shape pair, items per queue access, CTAs
+ * per SM) is chosen by the context's autotuner the first time a workload class is seen
+ * (keyed by SM count, patch set, largest window and stopping mode); that first call runs a few
+ * timed trials on a sample of the batch and synchronizes `stream`.
+ * rho, iters, box and opt apply to every image; opt->precision must be FP32 and
+ * opt->fp64_check is ignored.
+ * Errors: -1 on an invalid descriptor (as nlem_denoise), -5 for patch sizes other than 5 and 7
+ * or windows whose point count exceeds the batched kernel, -3 if the workspace cannot grow.
+ */
+int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, float rho, int iters,
+                       nlem_box box, const nlem_options* opt, void* stream);
+
+/* Text description of the launch shape the last nlem_denoise_batch call used (NUL-terminated,
+ * truncated to len).  Returns 0, or -1 if no batch has run. */
+int nlem_batch_config(nlem_ctx* ctx, char* buf, int len);
+
 /*
  * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an
  * FMA as 2 flops), from a register-only FMA-chain kernel timed with CUDA events; also

@@ -22,7 +22,9 @@ from ._binding import (  # noqa: F401
     em_solve_batch,
     lib_path,
     load_library,
+    nlem_batch_config,
     nlem_denoise,
+    nlem_denoise_batch,
     nlem_denoise_host,
     nlem_fp32_peak,
 )

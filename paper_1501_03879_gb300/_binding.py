@@ -27,6 +27,12 @@ class _Box(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float), ("hi", ctypes.c_float)]
 
 
+class _ImageDesc(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_void_p), ("out", ctypes.c_void_p), ("iters_used", ctypes.c_void_p),
+                ("residual", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("patch", ctypes.c_int), ("window", ctypes.c_int), ("h", ctypes.c_float)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
@@ -63,8 +69,10 @@ def load_library():
                                      vp, vp]
         lib.nlem_denoise_host.argtypes = [vp, vp, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp]
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
+        lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
-                     "nlem_denoise_host", "nlem_fp32_peak"):
+                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -267,3 +275,44 @@ def nlem_fp32_peak(ctx: Context | None = None):
     sms = ctypes.c_int()
     _check(load_library().nlem_fp32_peak(c.handle, ctypes.byref(tf), ctypes.byref(sms)))
     return tf.value, sms.value
+
+
+def nlem_denoise_batch(images, patches, windows, hs, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
+                       init=INIT_WEIGHTED_MEAN, ctx: Context | None = None, outs=None):
+    """NLEM on a list of float32 CUDA images of uneven sizes in one persistent launch
+    (CUDA-graph replayed).  patches, windows, hs: per-image patch size, window size and h.
+    Returns a list of dicts (out, iters_used, residual), one per image."""
+    import torch
+    n = len(images)
+    if not (len(patches) == len(windows) == len(hs) == n):
+        raise ValueError("one patch, window and h per image")
+    c = ctx or _ctx(images[0].device)
+    dev = images[0].device
+    if outs is None:
+        outs = [dict(out=torch.empty(im.shape, dtype=torch.float32, device=dev),
+                     iters_used=torch.empty(im.shape, dtype=torch.int32, device=dev),
+                     residual=torch.empty(im.shape, dtype=torch.float32, device=dev)) for im in images]
+    descs = (_ImageDesc * n)()
+    for k, im in enumerate(images):
+        _need(im, torch.float32, tuple(im.shape), f"images[{k}]")
+        H, W = im.shape
+        d = descs[k]
+        d.image = _ptr(im).value
+        d.out = _ptr(outs[k]["out"]).value
+        d.iters_used = _ptr(outs[k]["iters_used"]).value if outs[k].get("iters_used") is not None else None
+        d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
+        d.H, d.W, d.pitch = H, W, W
+        d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
+    o = _options(tol, check_every, PREC_FP32, init)
+    _check(load_library().nlem_denoise_batch(c.handle, descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
+                                             _stream(dev)))
+    return outs
+
+
+def nlem_batch_config(ctx: Context | None = None) -> str:
+    """Launch shape the autotuner chose for the last batch on this context."""
+    import torch
+    c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+    buf = ctypes.create_string_buffer(512)
+    _check(load_library().nlem_batch_config(c.handle, buf, 512))
+    return buf.value.decode()

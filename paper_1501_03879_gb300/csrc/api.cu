@@ -2,15 +2,30 @@
 // workspace ownership, dispatch to the kernels, and error reporting without exceptions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/nlem.h"
+#include "batch.h"
 #include "kernels.h"
+
+// A captured batch: the descriptors and parameters it was built for, the launch shape and the
+// instantiated graph (queue reset + persistent launch), which reads the workspace below.
+struct BatchPlan {
+  std::vector<nlemk::BatchImage> imgs;
+  nlemk::SolveParams prm{};
+  int init_mode = 0;
+  nlemk::BatchConfig cfg{};
+  long long total = 0;
+  cudaGraphExec_t exec = nullptr;
+};
 
 struct nlem_ctx {
   int device = 0;
@@ -20,6 +35,15 @@ struct nlem_ctx {
   float* ws_out = nullptr;
   int* ws_iters = nullptr;
   size_t ws_pixels = 0;
+  // workspace of the batched launch: image descriptors and the work-queue counter
+  nlemk::BatchImage* ws_batch = nullptr;
+  int ws_batch_cap = 0;
+  unsigned long long* ws_queue = nullptr;
+  cudaStream_t cap_stream = nullptr;                // private stream used for graph capture
+  std::map<std::string, nlemk::BatchConfig> tune;   // autotuner results by workload class
+  BatchPlan plan;
+  bool have_plan = false;
+  std::string last_cfg;
 };
 
 namespace {
@@ -119,9 +143,13 @@ int nlem_ctx_create(nlem_ctx** ctx, int device) {
 int nlem_ctx_destroy(nlem_ctx* ctx) {
   if (!ctx) return NLEM_OK;
   cudaSetDevice(ctx->device);
+  if (ctx->have_plan && ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   cudaFree(ctx->ws_img);
   cudaFree(ctx->ws_out);
   cudaFree(ctx->ws_iters);
+  cudaFree(ctx->ws_batch);
+  cudaFree(ctx->ws_queue);
   delete ctx;
   return NLEM_OK;
 }
@@ -263,6 +291,213 @@ int nlem_fp32_peak(nlem_ctx* ctx, double* tflops, int* sm_count) {
   int e = nlemk::measure_fp32_peak(ctx->sm_count, tflops);
   if (e != 0) return cuda_fail((cudaError_t)e, "fp32 peak probe");
   if (sm_count) *sm_count = ctx->sm_count;
+  return NLEM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Autotuner: time every launch shape on a strided sample of the batch (items 0, s, 2s, ...,
+// about 16k pixels) and keep the fastest.  Keyed by the workload class, not by the images.
+int autotune_batch(nlem_ctx* ctx, nlemk::BatchLaunch L, const std::string& key, cudaStream_t stream,
+                   nlemk::BatchConfig* best) {
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) {
+    *best = it->second;
+    return NLEM_OK;
+  }
+  const long long sample = 16384;
+  L.stride = std::max<long long>(1, L.total / sample);
+  static const int fetches[] = {1, 4, 16};
+  static const int ctas[] = {2, 1};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  nlemk::BatchConfig winner{0, 1, 2};
+  bool warmed = false;
+  for (int v = 0; v < nlemk::kBatchVariants; ++v) {
+    for (int f : fetches) {
+      for (int c : ctas) {
+        L.cfg = nlemk::BatchConfig{v, f, c};
+        for (int rep = warmed ? 0 : -1; rep < 1; ++rep) {   // one untimed warm-up run at first
+          cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), stream);
+          cudaEventRecord(e0, stream);
+          int rc = nlemk::launch_batch(L);
+          cudaEventRecord(e1, stream);
+          if (rc != 0) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail((cudaError_t)rc, "autotune launch");
+          }
+          cudaError_t e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune run");
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep == 0 && ms < best_ms) {
+            best_ms = ms;
+            winner = L.cfg;
+          }
+          warmed = true;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune[key] = winner;
+  *best = winner;
+  return NLEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, float rho, int iters, nlem_box box,
+                       const nlem_options* opt, void* stream) {
+  int rc = check_common(ctx, box, rho, iters, opt);
+  if (rc) return rc;
+  if (count < 0) return fail(NLEM_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return NLEM_OK;
+  if (!images) return fail(NLEM_ERR_INVALID, "images is NULL");
+  if (opt && opt->precision != NLEM_PREC_FP32)
+    return fail(NLEM_ERR_UNSUPPORTED, "the batched kernel computes weights in FP32 only");
+  std::vector<nlemk::BatchImage> imgs((size_t)count);
+  long long total = 0;
+  int maxS = 0, mask = 0;
+  for (int i = 0; i < count; ++i) {
+    const nlem_image_desc& d = images[i];
+    if (!d.image || !d.out) return fail(NLEM_ERR_INVALID, "image %d: image and out must be non-NULL", i);
+    if (d.H < 1 || d.W < 1 || d.pitch < d.W) return fail(NLEM_ERR_INVALID, "image %d: bad size %dx%d pitch %d", i, d.H, d.W, d.pitch);
+    if (d.patch < 1 || d.patch % 2 == 0 || d.window < 1 || d.window % 2 == 0)
+      return fail(NLEM_ERR_INVALID, "image %d: patch and window must be odd and >= 1", i);
+    if (d.patch > std::min(d.H, d.W)) return fail(NLEM_ERR_INVALID, "image %d: patch exceeds the image side", i);
+    if (!(d.h > 0.f) || !std::isfinite(d.h)) return fail(NLEM_ERR_INVALID, "image %d: h must be finite and > 0", i);
+    if (d.patch != 5 && d.patch != 7)
+      return fail(NLEM_ERR_UNSUPPORTED, "image %d: the batched kernel handles patch 5 and 7 (got %d)", i, d.patch);
+    if (d.window * d.window > std::min(nlemk::batch_max_points(d.patch, 0), nlemk::batch_max_points(d.patch, 1)) ||
+        !nlemk::batch_tile_fits(d.patch, d.window))
+      return fail(NLEM_ERR_UNSUPPORTED, "image %d: window %d too large for the batched kernel", i, d.window);
+    nlemk::BatchImage& b = imgs[(size_t)i];
+    b.img = d.image;
+    b.out = d.out;
+    b.iters = d.iters_used;
+    b.resid = d.residual;
+    b.H = d.H;
+    b.W = d.W;
+    b.pitch = d.pitch;
+    b.patch = d.patch;
+    b.S = d.window;
+    b.inv_h2 = 1.f / (d.h * d.h);
+    b.ih2 = 1.0 / ((double)d.h * (double)d.h);
+    b.pix_begin = total;
+    total += (long long)d.H * d.W;
+    maxS = std::max(maxS, d.window);
+    mask |= d.patch == 5 ? 1 : 2;
+  }
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  nlemk::SolveParams prm = make_params(box, rho, iters, opt, 0);
+  const int init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
+
+  const bool same = ctx->have_plan && ctx->plan.imgs.size() == imgs.size() &&
+                    std::memcmp(ctx->plan.imgs.data(), imgs.data(), imgs.size() * sizeof(nlemk::BatchImage)) == 0 &&
+                    std::memcmp(&ctx->plan.prm, &prm, sizeof(prm)) == 0 && ctx->plan.init_mode == init_mode;
+  if (!same) {
+    // drop the old plan, grow the workspace, upload the descriptors
+    if (ctx->have_plan && ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
+    ctx->have_plan = false;
+    if (count > ctx->ws_batch_cap) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->ws_batch);
+      ctx->ws_batch = nullptr;
+      ctx->ws_batch_cap = 0;
+      if (cudaMalloc(&ctx->ws_batch, sizeof(nlemk::BatchImage) * (size_t)count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NLEM_ERR_OOM, "batch workspace for %d images could not be allocated", count);
+      }
+      ctx->ws_batch_cap = count;
+    }
+    if (!ctx->ws_queue) {
+      if (cudaMalloc(&ctx->ws_queue, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NLEM_ERR_OOM, "work-queue counter could not be allocated");
+      }
+    }
+    if (!ctx->cap_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->ws_batch, imgs.data(), sizeof(nlemk::BatchImage) * (size_t)count,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "upload batch descriptors");
+    nlemk::BatchLaunch L{};
+    L.imgs = ctx->ws_batch;
+    L.count = count;
+    L.total = total;
+    L.stride = 1;
+    L.queue = ctx->ws_queue;
+    L.prm = prm;
+    L.init_mode = init_mode;
+    L.sm_count = ctx->sm_count;
+    L.stream = s;
+    char key[160];
+    std::snprintf(key, sizeof(key), "sm%d/patches%d/S%d/tol%d/it%d/init%d", ctx->sm_count, mask, maxS,
+                  prm.tol > 0.f ? 1 : 0, iters, init_mode);
+    nlemk::BatchConfig cfg{};
+    rc = autotune_batch(ctx, L, key, s, &cfg);
+    if (rc) return rc;
+    // capture queue reset + launch once on the private stream, after the upload completes
+    L.cfg = cfg;
+    L.stride = 1;
+    L.stream = ctx->cap_stream;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch set-up");
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
+    cudaMemsetAsync(ctx->ws_queue, 0, sizeof(unsigned long long), ctx->cap_stream);
+    int lrc = nlemk::launch_batch(L);
+    e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (lrc != 0) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail((cudaError_t)lrc, "capture batch launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end graph capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate batch graph");
+    ctx->plan.imgs = imgs;
+    ctx->plan.prm = prm;
+    ctx->plan.init_mode = init_mode;
+    ctx->plan.cfg = cfg;
+    ctx->plan.total = total;
+    ctx->plan.exec = exec;
+    ctx->have_plan = true;
+    char desc[256];
+    std::snprintf(desc, sizeof(desc), "%s; fetch=%d items; %d CTA/SM; %lld items; key %s",
+                  nlemk::batch_variant_name(cfg.variant), cfg.fetch, cfg.ctas_per_sm, total, key);
+    ctx->last_cfg = desc;
+  }
+  cudaError_t e = cudaGraphLaunch(ctx->plan.exec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launch batch graph");
+  return NLEM_OK;
+}
+
+int nlem_batch_config(nlem_ctx* ctx, char* buf, int len) {
+  if (!ctx || !buf || len < 1) return fail(NLEM_ERR_INVALID, "ctx and buf must be non-NULL, len >= 1");
+  if (!ctx->have_plan) {
+    buf[0] = 0;
+    return fail(NLEM_ERR_INVALID, "no batch has run on this context");
+  }
+  std::snprintf(buf, (size_t)len, "%s", ctx->last_cfg.c_str());
   return NLEM_OK;
 }
 

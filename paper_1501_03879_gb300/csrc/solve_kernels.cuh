@@ -112,126 +112,137 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
   return x < 0 ? -x : (x >= N ? 2 * N - 2 - x : x);
 }
 
+// One NLEM pixel (Sec. 3, Eq. L1regression) solved by the whole CTA: tile of the
+// reflect-padded image around the clipped search window -> patch rows in shared memory ->
+// weights exp(-||P_i-P_j||^2/h^2) -> start point -> EM-ADMM -> centre coordinate.
+// Ends with a barrier, so the caller may start the next pixel at once.
+template <class C, int K>
+__device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
+                           float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
+                           float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
+                           double* __restrict__ obj64, double* __restrict__ kkt64) {
+  static_assert(K * K == C::D, "patch size must match the compiled dimension");
+  const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
+  const bool last = (g == C::G - 1);
+  constexpr int HK = (K - 1) / 2;
+  const int R = (S - 1) / 2;
+  const int ir = (int)(pix / W), ic = (int)(pix - (long long)ir * W);
+  const int r0 = max(ir - R, 0), r1 = min(ir + R, H - 1);
+  const int c0 = max(ic - R, 0), c1 = min(ic + R, W - 1);
+  const int nwr = r1 - r0 + 1, nwc = c1 - c0 + 1, n = nwr * nwc;
+  const int TR = nwr + 2 * HK, TC = nwc + 2 * HK;
+  // tile rows r0-HK .. r1+HK, cols c0-HK .. c1+HK of the reflect-padded image
+  for (int i = t; i < TR * TC; i += C::NT) {
+    const int tr = i / TC, tc = i - tr * TC;
+    const int gr = reflect_idx(r0 - HK + tr, H), gc = reflect_idx(c0 - HK + tc, W);
+    sm.tile[i] = __ldg(img + (size_t)gr * pitch + gc);
+  }
+  for (int i = n * C::DP + t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
+  __syncthreads();
+  // patch rows: point j = window position (jr, jc) in row-major order, coordinate q = (qr, qc)
+  for (int idx = t; idx < n * C::D; idx += C::NT) {
+    const int j = idx / C::D, q = idx - j * C::D;
+    const int jr = j / nwc, jc = j - jr * nwc;
+    const int qr = q / K, qc = q - qr * K;
+    const int sg = q / C::Q, i = q - sg * C::Q;
+    sm.pts[j * C::DP + sg * C::QA + i] = sm.tile[(jr + qr) * TC + jc + qc];
+  }
+  // centre patch in slice layout (phantom slots zero)
+  for (int i = t; i < C::VEC; i += C::NT) {
+    const int sg = i / C::QA, slot = i - sg * C::QA;
+    float v = 0.f;
+    if (slot < slice_real<C>(sg, C::D)) {
+      const int q = sg * C::Q + slot;
+      const int qr = q / K, qc = q - qr * K;
+      v = sm.tile[(ir - r0 + qr) * TC + (ic - c0 + qc)];
+    }
+    sm.pcv[i] = v;
+  }
+  __syncthreads();
+  // weights (same lane layout as the solver)
+  float wreg[C::P];
+  {
+    float pc[C::Q];
+    load_slice<C>(sm.pcv + g * C::QA, last, pc);
+#pragma unroll
+    for (int p = 0; p < C::P; ++p) {
+      const int j = pg + p * C::NG;
+      const float* arow = sm.pts + j * C::DP + g * C::QA;
+      float D0 = 0.f, D1 = 0.f;
+#pragma unroll
+      for (int i = 0; i < C::NQA; ++i) {
+        const float4 a4 = load_quad<C>(arow, i, last);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int q = 4 * i + c;
+          if (q < C::Q) {
+            const float e = pc[q] - f4get(a4, c);
+            if (c & 1) D1 = fmaf(e, e, D1); else D0 = fmaf(e, e, D0);
+          }
+        }
+      }
+      const float Dp = point_sum<C>(D0 + D1);
+      const float w = j < n ? expf(-Dp * inv_h2) : 0.f;
+      wreg[p] = w;
+      if (g == 0) sm.lam[j] = w * prm.inv_mu;
+    }
+  }
+  if (init_mode == 1) {
+    for (int i = t; i < C::VEC; i += C::NT) {
+      const float z = clampf(sm.pcv[i], prm.lo, prm.hi);
+      const int sg = i / C::QA, slot = i - sg * C::QA;
+      const float zz = slot < slice_real<C>(sg, C::D) ? z : 0.f;
+      sm.zv[i] = zz;
+      sm.cv[i] = zz;
+      sm.sgv[i] = 0.f;
+    }
+    __syncthreads();
+  } else {
+    __syncthreads();   // lam visible, tile no longer needed (wred aliases it)
+    weighted_mean_start<C>(sm, wreg, n, C::D, prm);
+  }
+  admm_iterate<C>(sm, n, C::D, prm);
+  if (t == 0) {
+    constexpr int qc = (C::D - 1) / 2;
+    constexpr int sg = qc / C::Q, slot = qc - sg * C::Q;
+    out[pix] = sm.zv[sg * C::QA + slot];
+    if (iters_used) iters_used[pix] = (int)sm.scal[2];
+    if (resid) resid[pix] = sm.scal[3];
+  }
+  if (obj64 || kkt64) {
+    double F, Rk;
+    auto wfun = [&](int j) {
+      double D = 0.0;
+      for (int q = 0; q < C::D; ++q) {
+        const int sg = q / C::Q, i = q - sg * C::Q;
+        const double e = (double)sm.pcv[sg * C::QA + i] - (double)sm.pts[j * C::DP + sg * C::QA + i];
+        D += e * e;
+      }
+      return exp(-D * ih2);
+    };
+    fp64_check<C>(sm, n, C::D, prm, wfun, F, Rk);
+    if (t == 0) {
+      if (obj64) obj64[pix] = F;
+      if (kkt64) kkt64[pix] = Rk;
+    }
+  }
+  __syncthreads();
+}
+
 template <class C, int K>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
             float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64) {
-  static_assert(K * K == C::D, "patch size must match the compiled dimension");
   extern __shared__ float4 smem_raw[];
   Smem<C> sm(reinterpret_cast<float*>(smem_raw));
-  const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
-  const bool last = (g == C::G - 1);
-  constexpr int HK = (K - 1) / 2;
-  const int R = (S - 1) / 2;
   const long long npix = (long long)H * W;
-  for (long long pix = blockIdx.x; pix < npix; pix += gridDim.x) {
-    const int ir = (int)(pix / W), ic = (int)(pix - (long long)ir * W);
-    const int r0 = max(ir - R, 0), r1 = min(ir + R, H - 1);
-    const int c0 = max(ic - R, 0), c1 = min(ic + R, W - 1);
-    const int nwr = r1 - r0 + 1, nwc = c1 - c0 + 1, n = nwr * nwc;
-    const int TR = nwr + 2 * HK, TC = nwc + 2 * HK;
-    // tile rows r0-HK .. r1+HK, cols c0-HK .. c1+HK of the reflect-padded image
-    for (int i = t; i < TR * TC; i += C::NT) {
-      const int tr = i / TC, tc = i - tr * TC;
-      const int gr = reflect_idx(r0 - HK + tr, H), gc = reflect_idx(c0 - HK + tc, W);
-      sm.tile[i] = __ldg(img + (size_t)gr * pitch + gc);
-    }
-    for (int i = n * C::DP + t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
-    __syncthreads();
-    // patch rows: point j = window position (jr, jc) in row-major order, coordinate q = (qr, qc)
-    for (int idx = t; idx < n * C::D; idx += C::NT) {
-      const int j = idx / C::D, q = idx - j * C::D;
-      const int jr = j / nwc, jc = j - jr * nwc;
-      const int qr = q / K, qc = q - qr * K;
-      const int sg = q / C::Q, i = q - sg * C::Q;
-      sm.pts[j * C::DP + sg * C::QA + i] = sm.tile[(jr + qr) * TC + jc + qc];
-    }
-    // centre patch in slice layout (phantom slots zero)
-    for (int i = t; i < C::VEC; i += C::NT) {
-      const int sg = i / C::QA, slot = i - sg * C::QA;
-      float v = 0.f;
-      if (slot < slice_real<C>(sg, C::D)) {
-        const int q = sg * C::Q + slot;
-        const int qr = q / K, qc = q - qr * K;
-        v = sm.tile[(ir - r0 + qr) * TC + (ic - c0 + qc)];
-      }
-      sm.pcv[i] = v;
-    }
-    __syncthreads();
-    // weights (same lane layout as the solver)
-    float wreg[C::P];
-    {
-      float pc[C::Q];
-      load_slice<C>(sm.pcv + g * C::QA, last, pc);
-#pragma unroll
-      for (int p = 0; p < C::P; ++p) {
-        const int j = pg + p * C::NG;
-        const float* arow = sm.pts + j * C::DP + g * C::QA;
-        float D0 = 0.f, D1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < C::NQA; ++i) {
-          const float4 a4 = load_quad<C>(arow, i, last);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int q = 4 * i + c;
-            if (q < C::Q) {
-              const float e = pc[q] - f4get(a4, c);
-              if (c & 1) D1 = fmaf(e, e, D1); else D0 = fmaf(e, e, D0);
-            }
-          }
-        }
-        const float Dp = point_sum<C>(D0 + D1);
-        const float w = j < n ? expf(-Dp * inv_h2) : 0.f;
-        wreg[p] = w;
-        if (g == 0) sm.lam[j] = w * prm.inv_mu;
-      }
-    }
-    if (init_mode == 1) {
-      for (int i = t; i < C::VEC; i += C::NT) {
-        const float z = clampf(sm.pcv[i], prm.lo, prm.hi);
-        const int sg = i / C::QA, slot = i - sg * C::QA;
-        const float zz = slot < slice_real<C>(sg, C::D) ? z : 0.f;
-        sm.zv[i] = zz;
-        sm.cv[i] = zz;
-        sm.sgv[i] = 0.f;
-      }
-      __syncthreads();
-    } else {
-      __syncthreads();   // lam visible, tile no longer needed (wred aliases it)
-      weighted_mean_start<C>(sm, wreg, n, C::D, prm);
-    }
-    admm_iterate<C>(sm, n, C::D, prm);
-    if (t == 0) {
-      constexpr int qc = (C::D - 1) / 2;
-      constexpr int sg = qc / C::Q, slot = qc - sg * C::Q;
-      out[pix] = sm.zv[sg * C::QA + slot];
-      if (iters_used) iters_used[pix] = (int)sm.scal[2];
-      if (resid) resid[pix] = sm.scal[3];
-    }
-    if (obj64 || kkt64) {
-      double F, Rk;
-      auto wfun = [&](int j) {
-        double D = 0.0;
-        for (int q = 0; q < C::D; ++q) {
-          const int sg = q / C::Q, i = q - sg * C::Q;
-          const double e = (double)sm.pcv[sg * C::QA + i] - (double)sm.pts[j * C::DP + sg * C::QA + i];
-          D += e * e;
-        }
-        return exp(-D * ih2);
-      };
-      fp64_check<C>(sm, n, C::D, prm, wfun, F, Rk);
-      if (t == 0) {
-        if (obj64) obj64[pix] = F;
-        if (kkt64) kkt64[pix] = Rk;
-      }
-    }
-    __syncthreads();
-  }
+  for (long long pix = blockIdx.x; pix < npix; pix += gridDim.x)
+    nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64);
 }
 
 // ------------------------------------------------------------------------------------------
-// dispatch tables
+// launchers
 // ------------------------------------------------------------------------------------------
 template <class C>
 inline int launch_em(const EmLaunch& L, int grid_mult) {
