@@ -167,6 +167,29 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
 int nlem_batch_config(nlem_ctx* ctx, char* buf, int len);
 
 /*
+ * nlem_denoise_batch_noalloc - nlem_denoise_batch for callers that cannot allocate device
+ * memory: code that runs inside another framework's allocator or memory pool, or under a
+ * memory budget in which every device allocation belongs to the host application, and so may
+ * not call cudaMalloc (or anything that does) behind its back.  No paper counterpart: the
+ * method itself needs no allocation; this entry point only moves the batched launch's scratch
+ * (its work-queue counter and image descriptors) into a fixed array that the library holds.
+ *   - Makes no device (or heap) allocation and needs no nlem_ctx; runs on the current device
+ *     and `stream`; images as for nlem_denoise_batch (patch 5 or 7, window^2 <= 441).
+ *   - At most NLEM_NOALLOC_MAX_IMAGES images per call (-1 above that).  The array
+ *     (about 18 KB) stays resident on every GPU that loads the library until the process exits.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture on that device.
+ *   - Every call shares the one array: the descriptors are rewritten and the counter is reset
+ *     on each call, so calls whose GPU work overlaps (different streams, or different host
+ *     threads, with no ordering between them) race and corrupt each other.  Order them.
+ *   - Uses a fixed launch shape (no autotuning, no CUDA graph).
+ * Errors as nlem_denoise_batch; messages via nlem_last_error().
+ */
+#define NLEM_NOALLOC_MAX_IMAGES 256
+int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int count, float rho, int iters,
+                               nlem_box box, const nlem_options* opt, void* stream);
+
+/*
  * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an
  * FMA as 2 flops), from a register-only FMA-chain kernel timed with CUDA events; also
  * returns the SM count.  Used as the roofline denominator of the ALU-bound kernels.

@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     nlem_batch_config,
     nlem_denoise,
     nlem_denoise_batch,
+    nlem_denoise_batch_noalloc,
     nlem_denoise_host,
     nlem_fp32_peak,
 )

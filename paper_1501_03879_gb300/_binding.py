@@ -71,8 +71,10 @@ def load_library():
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
+        lib.nlem_denoise_batch_noalloc.argtypes = [ctypes.POINTER(_ImageDesc), i, f, i, _Box,
+                                                   ctypes.POINTER(_Options), vp]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
-                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config"):
+                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -316,3 +318,30 @@ def nlem_batch_config(ctx: Context | None = None) -> str:
     buf = ctypes.create_string_buffer(512)
     _check(load_library().nlem_batch_config(c.handle, buf, 512))
     return buf.value.decode()
+
+
+def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
+                               check_every=1, init=INIT_WEIGHTED_MEAN):
+    """nlem_denoise_batch without any device allocation: the caller supplies every output
+    buffer (`outs`: one dict per image with out [H,W] and optionally iters_used, residual);
+    the library uses its own fixed scratch array.  At most 256 images per call; calls whose GPU
+    work overlaps must not run concurrently (they share that array)."""
+    import torch
+    n = len(images)
+    if not (len(patches) == len(windows) == len(hs) == len(outs) == n):
+        raise ValueError("one patch, window, h and output dict per image")
+    descs = (_ImageDesc * n)()
+    for k, im in enumerate(images):
+        _need(im, torch.float32, tuple(im.shape), f"images[{k}]")
+        H, W = im.shape
+        d = descs[k]
+        d.image = _ptr(im).value
+        d.out = _ptr(outs[k]["out"]).value
+        d.iters_used = _ptr(outs[k]["iters_used"]).value if outs[k].get("iters_used") is not None else None
+        d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
+        d.H, d.W, d.pitch = H, W, W
+        d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
+    o = _options(tol, check_every, PREC_FP32, init)
+    _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
+                                                     _stream(images[0].device)))
+    return outs

@@ -105,6 +105,10 @@ int set_device(nlem_ctx* ctx) {
 
 }  // namespace
 
+namespace nlemk {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace nlemk
+
 extern "C" {
 
 void nlem_options_default(nlem_options* opt) {

@@ -44,6 +44,9 @@ int launch_nlem_fp32(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
 
+// Sets the calling thread's message returned by nlem_last_error().
+void set_last_error(const char* msg);
+
 // FP32 FMA-chain throughput probe; returns cudaError_t.
 int measure_fp32_peak(int sm_count, double* tflops);
 
