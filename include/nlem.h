@@ -115,7 +115,11 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
  *   image [H][pitch] float32 (device), pitch >= W elements
  *   out   [H][W] float32 (device)
  *   iters_used [H][W] int32 or NULL;  residual [H][W] float32 or NULL (as em_solve_batch)
- *   obj64 / kkt64 [H][W] double or NULL (opt->fp64_check)
+ *   obj64 / kkt64 [H][W] double or NULL (opt->fp64_check; weights recomputed in FP64)
+ * opt->precision = NLEM_PREC_BF16: the cross terms <P_i, P_j> of the squared distances
+ * ||P_i||^2 + ||P_j||^2 - 2 <P_i, P_j> are computed from bfloat16-rounded patches on the
+ * tensor cores (tcgen05, FP32 accumulation), the norms in FP32, into a context-owned weight
+ * table; the ADMM iterations stay in FP32.  Patch 5, 7 or 9.
  * Errors: -1 if patch or window is even or < 1, patch > min(H, W),
  * h <= 0, rho <= 0, iters < 0, lo > hi; -5 if patch*patch > 128 or the window holds more
  * points than the kernels support (window <= 31).
@@ -188,6 +192,25 @@ int nlem_batch_config(nlem_ctx* ctx, char* buf, int len);
 #define NLEM_NOALLOC_MAX_IMAGES 256
 int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int count, float rho, int iters,
                                nlem_box box, const nlem_options* opt, void* stream);
+
+/*
+ * nlem_bf16_weights - the weight stage of the mixed-precision path on its own: for every
+ * pixel i and every centre j of its clipped search window, in NLEM's window order,
+ *   wtab[i * window^2 + j] = exp(-(||P_i||^2 + ||P_j||^2 - 2 <bf16(P_i), bf16(P_j)>) / h^2)
+ * (Sec. 3's weights with the cross term from bfloat16-rounded patches on the tensor cores,
+ * FP32 accumulation; norms in FP32; negative squared distances from rounding become 0).
+ * wtab: device [H*W][window^2] float32; entries j >= the pixel's window size are not written.
+ * Patch 5, 7 or 9; window <= 31.  A bounded-wait timeout is reported by nlem_device_status.
+ */
+int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch,
+                      int window, float h, float* wtab, void* stream);
+
+/*
+ * nlem_device_status - waits for the device and reports faults the kernels detected on their
+ * own: NLEM_ERR_TIMEOUT if a bounded wait of the BF16 tensor-core weight kernel ran out (the
+ * flag is then cleared), NLEM_ERR_CUDA for a CUDA error, 0 otherwise.
+ */
+int nlem_device_status(nlem_ctx* ctx);
 
 /*
  * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an

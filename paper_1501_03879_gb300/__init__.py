@@ -23,9 +23,11 @@ from ._binding import (  # noqa: F401
     lib_path,
     load_library,
     nlem_batch_config,
+    nlem_bf16_weights,
     nlem_denoise,
     nlem_denoise_batch,
     nlem_denoise_batch_noalloc,
     nlem_denoise_host,
+    nlem_device_status,
     nlem_fp32_peak,
 )

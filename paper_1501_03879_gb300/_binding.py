@@ -71,10 +71,13 @@ def load_library():
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
+        lib.nlem_device_status.argtypes = [vp]
+        lib.nlem_bf16_weights.argtypes = [vp, vp, i, i, i, i, i, f, vp, vp]
         lib.nlem_denoise_batch_noalloc.argtypes = [ctypes.POINTER(_ImageDesc), i, f, i, _Box,
                                                    ctypes.POINTER(_Options), vp]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
-                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc"):
+                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc",
+                     "nlem_device_status", "nlem_bf16_weights"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -345,3 +348,24 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
     _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
                                                      _stream(images[0].device)))
     return outs
+
+
+def nlem_device_status(ctx: Context | None = None) -> int:
+    """Synchronize and raise NlemError if a kernel reported a bounded-wait timeout."""
+    import torch
+    c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+    return _check(load_library().nlem_device_status(c.handle))
+
+
+def nlem_bf16_weights(image, patch=9, window=21, h=300.0, ctx: Context | None = None, out=None):
+    """Mixed-precision weight table [H*W, window^2] of a float32 CUDA image (tensor-core cross
+    terms); entries past a pixel's clipped window size are left as they were in `out`."""
+    import torch
+    H, W = image.shape
+    _need(image, torch.float32, (H, W), "image")
+    c = ctx or _ctx(image.device)
+    if out is None:
+        out = torch.full((H * W, window * window), float("nan"), dtype=torch.float32, device=image.device)
+    _check(load_library().nlem_bf16_weights(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+                                            _ptr(out), _stream(image.device)))
+    return out

@@ -35,6 +35,11 @@ struct nlem_ctx {
   float* ws_out = nullptr;
   int* ws_iters = nullptr;
   size_t ws_pixels = 0;
+  // workspace of the mixed-precision path: weight table [pixel][window index] and the flag the
+  // tensor-core kernel raises if one of its bounded waits runs out
+  float* ws_wtab = nullptr;
+  size_t ws_wtab_floats = 0;
+  int* ws_err = nullptr;
   // workspace of the batched launch: image descriptors and the work-queue counter
   nlemk::BatchImage* ws_batch = nullptr;
   int ws_batch_cap = 0;
@@ -154,6 +159,8 @@ int nlem_ctx_destroy(nlem_ctx* ctx) {
   cudaFree(ctx->ws_iters);
   cudaFree(ctx->ws_batch);
   cudaFree(ctx->ws_queue);
+  cudaFree(ctx->ws_wtab);
+  cudaFree(ctx->ws_err);
   delete ctx;
   return NLEM_OK;
 }
@@ -214,8 +221,6 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   if (patch > side) return fail(NLEM_ERR_INVALID, "patch %d exceeds the image side %d", patch, side);
   if (!(h > 0.f) || !finite(h)) return fail(NLEM_ERR_INVALID, "h must be finite and > 0 (got %g)", h);
   if (!image || !out) return fail(NLEM_ERR_INVALID, "image and out must be non-NULL");
-  if (opt && opt->precision == NLEM_PREC_BF16)
-    return fail(NLEM_ERR_UNSUPPORTED, "BF16 cross-term weights are not built into this library");
   if (patch * patch > 128) return fail(NLEM_ERR_UNSUPPORTED, "patch^2 must be <= 128");
   int cap = nlemk::nlem_capacity(patch);
   if (cap == 0) return fail(NLEM_ERR_UNSUPPORTED, "patch %d not compiled (5, 7, 9 are)", patch);
@@ -242,6 +247,34 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   L.kkt64 = chk ? kkt64 : nullptr;
   L.sm_count = ctx->sm_count;
   L.stream = (cudaStream_t)stream;
+  L.wtab = nullptr;
+  if (opt && opt->precision == NLEM_PREC_BF16) {
+    // cross terms on the tensor cores into the weight table, then the solver reads it
+    const size_t need = (size_t)H * W * (size_t)window * window;
+    if (need > ctx->ws_wtab_floats) {
+      cudaStreamSynchronize((cudaStream_t)stream);
+      cudaFree(ctx->ws_wtab);
+      ctx->ws_wtab = nullptr;
+      ctx->ws_wtab_floats = 0;
+      if (cudaMalloc(&ctx->ws_wtab, need * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NLEM_ERR_OOM, "weight table of %zu floats could not be allocated", need);
+      }
+      ctx->ws_wtab_floats = need;
+    }
+    if (!ctx->ws_err) {
+      if (cudaMalloc(&ctx->ws_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NLEM_ERR_OOM, "status flag could not be allocated");
+      }
+      cudaMemset(ctx->ws_err, 0, sizeof(int));
+    }
+    int we = nlemk::launch_bf16_weights(image, H, W, pitch, patch, window, L.inv_h2, ctx->ws_wtab, ctx->ws_err,
+                                        (cudaStream_t)stream);
+    if (we == -1) return fail(NLEM_ERR_UNSUPPORTED, "BF16 weights are compiled for patch 5, 7 and 9 with window <= 31");
+    if (we != 0) return cuda_fail((cudaError_t)we, "BF16 weight kernel launch");
+    L.wtab = ctx->ws_wtab;
+  }
   int e = nlemk::launch_nlem_fp32(L);
   if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for patch %d, window %d", patch, window);
   if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise launch");
@@ -285,6 +318,48 @@ int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int 
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "nlem_denoise_host");
+  return NLEM_OK;
+}
+
+int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                      float* wtab, void* stream) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  if (!image || !wtab) return fail(NLEM_ERR_INVALID, "image and wtab must be non-NULL");
+  if (H < 1 || W < 1 || pitch < W) return fail(NLEM_ERR_INVALID, "bad image size or pitch");
+  if (patch < 1 || patch % 2 == 0 || window < 1 || window % 2 == 0)
+    return fail(NLEM_ERR_INVALID, "patch and window must be odd and >= 1");
+  if (patch > std::min(H, W)) return fail(NLEM_ERR_INVALID, "patch exceeds the image side");
+  if (!(h > 0.f) || !std::isfinite(h)) return fail(NLEM_ERR_INVALID, "h must be finite and > 0");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  if (!ctx->ws_err) {
+    if (cudaMalloc(&ctx->ws_err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(NLEM_ERR_OOM, "status flag could not be allocated");
+    }
+    cudaMemset(ctx->ws_err, 0, sizeof(int));
+  }
+  int we = nlemk::launch_bf16_weights(image, H, W, pitch, patch, window, 1.f / (h * h), wtab, ctx->ws_err,
+                                      (cudaStream_t)stream);
+  if (we == -1) return fail(NLEM_ERR_UNSUPPORTED, "BF16 weights are compiled for patch 5, 7 and 9 with window <= 31");
+  if (we != 0) return cuda_fail((cudaError_t)we, "BF16 weight kernel launch");
+  return NLEM_OK;
+}
+
+int nlem_device_status(nlem_ctx* ctx) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+  if (!ctx->ws_err) return NLEM_OK;
+  int flag = 0;
+  e = cudaMemcpy(&flag, ctx->ws_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status flag");
+  if (flag) {
+    cudaMemset(ctx->ws_err, 0, sizeof(int));
+    return fail(NLEM_ERR_TIMEOUT, "a bounded tensor-core wait ran out; affected weights were not written");
+  }
   return NLEM_OK;
 }
 

@@ -34,9 +34,15 @@ struct NlemLaunch {
   float* resid;
   double* obj64;
   double* kkt64;
+  const float* wtab;     // precomputed weights [pixel][window index] or NULL
   int sm_count;
   cudaStream_t stream;
 };
+
+// BF16 tensor-core cross terms -> weight table wtab [H*W][S*S]; err set to 1 if an MMA wait
+// ran out.  Returns cudaError_t, or -1 for an uncompiled patch size.
+int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, int S, float inv_h2, float* wtab,
+                        int* err, cudaStream_t stream);
 
 // Return cudaError_t codes (0 = launched), or -1 when no compiled shape holds the problem.
 int launch_em_batch(const EmLaunch& L);

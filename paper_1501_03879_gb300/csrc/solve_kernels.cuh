@@ -120,7 +120,8 @@ template <class C, int K>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
-                           double* __restrict__ obj64, double* __restrict__ kkt64) {
+                           double* __restrict__ obj64, double* __restrict__ kkt64,
+                           const float* __restrict__ wtab = nullptr) {
   static_assert(K * K == C::D, "patch size must match the compiled dimension");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
   const bool last = (g == C::G - 1);
@@ -182,7 +183,8 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
         }
       }
       const float Dp = point_sum<C>(D0 + D1);
-      const float w = j < n ? expf(-Dp * inv_h2) : 0.f;
+      float w = j < n ? expf(-Dp * inv_h2) : 0.f;
+      if (wtab) w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;   // precomputed (BF16 mode)
       wreg[p] = w;
       if (g == 0) sm.lam[j] = w * prm.inv_mu;
     }
@@ -233,12 +235,14 @@ template <class C, int K>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
-            float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64) {
+            float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64,
+            const float* __restrict__ wtab) {
   extern __shared__ float4 smem_raw[];
   Smem<C> sm(reinterpret_cast<float*>(smem_raw));
   const long long npix = (long long)H * W;
   for (long long pix = blockIdx.x; pix < npix; pix += gridDim.x)
-    nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64);
+    nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
+                     wtab);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -271,7 +275,7 @@ inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.img, L.H, L.W, L.pitch, L.S, L.inv_h2, L.inv_h2_exact, L.prm,
                                                           L.init_mode, L.out, L.iters_used, L.resid, L.obj64,
-                                                          L.kkt64);
+                                                          L.kkt64, L.wtab);
   return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,77 @@
+"""GPU parity of the mixed-precision path: BF16 cross terms on the tensor cores (tcgen05) for
+the NLEM weights, FP32 ADMM.  Checked against the oracle's model of the same arithmetic
+(cross term from bfloat16-rounded patches, everything else exact), which separates the weight
+error from the iteration error; the error against the exact FP64 oracle is reported."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+DEV = "cuda:0"
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1501_03879_gb300 as m
+    m.load_library()
+    return m
+
+
+@pytest.mark.parametrize("H,W,k,S", [(19, 23, 9, 11), (40, 36, 9, 21), (33, 17, 7, 13), (24, 40, 5, 21)])
+def test_weight_table_matches_bf16_model(nl, H, W, k, S):
+    g, _ = synth.noisy_image(7000 + H + W, H, W, 30.0, salt_pepper=0.05)
+    h = 300.0
+    wt = nl.nlem_bf16_weights(torch.from_numpy(g).to(DEV), patch=k, window=S, h=h).cpu().numpy()
+    nl.nlem_device_status()
+    for lin in [0, W - 1, (H // 2) * W + W // 3, H * W - 1, 5 * W + 7]:
+        _, w_model, _ = oracle.nlem_problem(g, k, S, h, lin, weight_mode=1)
+        _, w_exact, _ = oracle.nlem_problem(g, k, S, h, lin, weight_mode=0)
+        got = wt[lin, :len(w_model)]
+        # same arithmetic up to FP32 norms and accumulation order
+        assert np.max(np.abs(got - w_model)) <= 2e-5 + 2e-5 * np.max(w_model), (lin, np.max(np.abs(got - w_model)))
+        # and close to the exact weights (bfloat16 keeps 8 bits: a few percent on D)
+        assert np.max(np.abs(got - w_exact)) <= 0.1
+
+
+def test_bf16_nlem_matches_oracle_bf16_model(nl):
+    g, f = synth.noisy_image(7100, 36, 40, 30.0, salt_pepper=0.05)
+    r = nl.nlem_denoise(torch.from_numpy(g).to(DEV), patch=9, window=11, h=300.0, rho=1.0, iters=60,
+                        precision=nl.PREC_BF16)
+    nl.nlem_device_status()
+    got = r["out"].cpu().numpy()
+    ref_model = oracle.nlem(g, 9, 11, 300.0, 1.0, 60, weight_mode=1)["out"]
+    ref_exact = oracle.nlem(g, 9, 11, 300.0, 1.0, 60, weight_mode=0)["out"]
+    assert rel_err(got, ref_model).max() <= TOL
+    # error against the exact FP64 oracle (bfloat16 keeps 8 significant bits of the cross
+    # term, which cancels against the norms): reported, with a loose bound
+    e_exact = rel_err(got, ref_exact)
+    print(f"BF16 NLEM vs exact FP64 oracle: max rel {e_exact.max():.3e}, mean {e_exact.mean():.3e}")
+    assert e_exact.max() <= 5e-2
+
+
+def test_bf16_full_size_crop(nl):
+    """1024x1024, sigma=30 plus 5% salt-and-pepper, 9x9 patches, 21x21 window, h=300, rho=1,
+    100 iterations: a centre crop of the output against the oracle (both weight models)."""
+    g, f = synth.noisy_image(1003, 1024, 1024, 30.0, salt_pepper=0.05)
+    r = nl.nlem_denoise(torch.from_numpy(g).to(DEV), patch=9, window=21, h=300.0, rho=1.0, iters=100,
+                        precision=nl.PREC_BF16)
+    nl.nlem_device_status()
+    out = r["out"].cpu().numpy()
+    rows, cols = np.meshgrid(np.arange(496, 528), np.arange(496, 528), indexing="ij")
+    pix = (rows * 1024 + cols).reshape(-1)
+    ref = oracle.nlem(g, 9, 21, 300.0, 1.0, 100, weight_mode=1, pixels=pix)["out"]
+    assert rel_err(out.reshape(-1)[pix], ref).max() <= TOL
+    assert synth.psnr(out, f) > synth.psnr(g, f) + 5
