@@ -33,6 +33,9 @@ PINS = {
     "nlem": "patch/weight assembly against numpy.pad reflect; constant image; S=1; k=1 weighted median",
     "irls": "surrogate stationarity; converges to the EM within sqrt(eps)-scale",
     "weiszfeld": "objective non-increasing; agrees with ADMM at convergence",
+    "features": "weighted median: dominant weight, equal weights (ordinary median), d=1 problem (1) "
+                "solution; entropy of uniform weights = log n; weighted mean = 1-point mean",
+    "mlp": "loss gradient against central finite differences of the loss",
 }
 
 _lib = None
@@ -82,6 +85,10 @@ def _load():
     lib.orc_nlem_problem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_ll, c_int, D, D, D]
     lib.orc_nlem_problem.restype = c_int
     lib.orc_num_cores.restype = c_int
+    lib.orc_features.argtypes = [D, D, c_int, c_int, D]
+    lib.orc_mlp_forward.argtypes = [D, c_int, c_int, c_double, D, c_ll, D]
+    lib.orc_mlp_loss_grad.argtypes = [D, c_int, c_int, c_double, D, D, c_ll, D]
+    lib.orc_mlp_loss_grad.restype = c_double
     _lib = lib
     return lib
 
@@ -250,3 +257,36 @@ def nlem_problem(img, k, S, h, lin, weight_mode=0):
     n = _load().orc_nlem_problem(_fp(img), H, W, int(k), int(S), float(h), int(lin), int(weight_mode),
                                  _dp(pts), _dp(w), _dp(pc))
     return pts[:n].copy(), w[:n].copy(), pc
+
+
+def features(pts, w):
+    """[m (d), q (d), H, pmax] of one problem (weighted mean, coordinate-wise lower weighted
+    median, weight entropy, largest normalised weight)."""
+    pts, w = _f64(pts), _f64(w)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    n, d = pts.shape
+    f = np.empty(2 * d + 2)
+    _load().orc_features(_dp(pts), _dp(w), n, d, _dp(f))
+    return f
+
+
+def mlp_num_params(d, hidden=128):
+    F, O = 2 * d + 2, d + 1
+    return hidden * F + hidden + hidden * hidden + hidden + O * hidden + O
+
+
+def mlp_forward(params, d, feats, hidden=128, nref=441.0):
+    params, feats = _f64(params), _f64(feats)
+    B = feats.shape[0]
+    y = np.empty((B, d + 1))
+    _load().orc_mlp_forward(_dp(params), d, hidden, float(nref), _dp(feats), B, _dp(y))
+    return y
+
+
+def mlp_loss_grad(params, d, feats, targets, hidden=128, nref=441.0):
+    params, feats, targets = _f64(params), _f64(feats), _f64(targets)
+    B = feats.shape[0]
+    g = np.empty_like(params)
+    L = _load().orc_mlp_loss_grad(_dp(params), d, hidden, float(nref), _dp(feats), _dp(targets), B, _dp(g))
+    return float(L), g

@@ -565,3 +565,165 @@ int orc_nlem_problem(const float *img, int H, int W, int k, int S, double h, lon
     }
   return n;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper): problem features and a small MLP, for checking the
+ * GPU feature, forward and backward kernels.
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct {
+  double v, w;
+} vw_pair;
+
+static int cmp_vw(const void *a, const void *b) {
+  double x = ((const vw_pair *)a)->v, y = ((const vw_pair *)b)->v;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Features of problem (1): f = [m (d), q (d), H, pmax] with p_k = w_k / sum w,
+ * m = sum p_k a_k (weighted mean, not projected), q_c = lower weighted median of coordinate c
+ * (the smallest value whose cumulative weight in ascending order reaches half the total),
+ * H = -sum_{p_k > 0} p_k log p_k, pmax = max p_k.  All weights zero: p uniform. */
+void orc_features(const double *pts, const double *w, int n, int d, double *f) {
+  double W = 0.0;
+  for (int k = 0; k < n; ++k) W += w[k];
+  vw_pair *buf = (vw_pair *)malloc(sizeof(vw_pair) * (size_t)n);
+  for (int c = 0; c < d; ++c) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += (W > 0.0 ? w[k] / W : 1.0 / n) * pts[(size_t)k * d + c];
+    f[c] = s;
+    for (int k = 0; k < n; ++k) {
+      buf[k].v = pts[(size_t)k * d + c];
+      buf[k].w = W > 0.0 ? w[k] : 1.0;
+    }
+    qsort(buf, (size_t)n, sizeof(vw_pair), cmp_vw);
+    double tot = 0.0, cum = 0.0;
+    for (int k = 0; k < n; ++k) tot += buf[k].w;
+    double med = buf[n - 1].v;
+    for (int k = 0; k < n; ++k) {
+      cum += buf[k].w;
+      if (cum >= 0.5 * tot) {
+        med = buf[k].v;
+        break;
+      }
+    }
+    f[d + c] = med;
+  }
+  double H = 0.0, pmax = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double p = W > 0.0 ? w[k] / W : 1.0 / n;
+    if (p > 0.0) H -= p * log(p);
+    if (p > pmax) pmax = p;
+  }
+  f[2 * d] = H;
+  f[2 * d + 1] = pmax;
+  free(buf);
+}
+
+/* MLP  x = normalise(f);  h1 = relu(W1 x + b1);  h2 = relu(W2 h1 + b2);  y = W3 h2 + b3
+ * with F = 2d+2 inputs, Hd hidden units, O = d+1 outputs.  normalise: coordinates of m and q
+ * -> (v - 127.5) / 64, H -> H / log(nref), pmax unchanged.
+ * Parameter vector (row-major): W1 [Hd][F], b1 [Hd], W2 [Hd][Hd], b2 [Hd], W3 [O][Hd], b3 [O].
+ * Loss of a batch: L = (1/B) sum_b [ (1/d) sum_{c<d} (y_bc - t_bc)^2 + (y_bd - t_bd)^2 ]. */
+static void mlp_normalise(const double *f, int d, double nref, double *x) {
+  for (int c = 0; c < 2 * d; ++c) x[c] = (f[c] - 127.5) / 64.0;
+  x[2 * d] = f[2 * d] / log(nref);
+  x[2 * d + 1] = f[2 * d + 1];
+}
+
+void orc_mlp_forward(const double *prm, int d, int Hd, double nref, const double *f, long long B, double *y) {
+  int F = 2 * d + 2, O = d + 1;
+  const double *W1 = prm, *b1 = W1 + (size_t)Hd * F, *W2 = b1 + Hd, *b2 = W2 + (size_t)Hd * Hd;
+  const double *W3 = b2 + Hd, *b3 = W3 + (size_t)O * Hd;
+  double *x = (double *)malloc(sizeof(double) * (size_t)F);
+  double *h1 = (double *)malloc(sizeof(double) * (size_t)Hd);
+  double *h2 = (double *)malloc(sizeof(double) * (size_t)Hd);
+  for (long long b = 0; b < B; ++b) {
+    mlp_normalise(f + (size_t)b * F, d, nref, x);
+    for (int i = 0; i < Hd; ++i) {
+      double s = b1[i];
+      for (int j = 0; j < F; ++j) s += W1[(size_t)i * F + j] * x[j];
+      h1[i] = s > 0.0 ? s : 0.0;
+    }
+    for (int i = 0; i < Hd; ++i) {
+      double s = b2[i];
+      for (int j = 0; j < Hd; ++j) s += W2[(size_t)i * Hd + j] * h1[j];
+      h2[i] = s > 0.0 ? s : 0.0;
+    }
+    for (int i = 0; i < O; ++i) {
+      double s = b3[i];
+      for (int j = 0; j < Hd; ++j) s += W3[(size_t)i * Hd + j] * h2[j];
+      y[(size_t)b * O + i] = s;
+    }
+  }
+  free(x); free(h1); free(h2);
+}
+
+/* Loss and its gradient with respect to every parameter (backpropagation, FP64). */
+double orc_mlp_loss_grad(const double *prm, int d, int Hd, double nref, const double *f, const double *t,
+                         long long B, double *grad) {
+  int F = 2 * d + 2, O = d + 1;
+  size_t P = (size_t)Hd * F + Hd + (size_t)Hd * Hd + Hd + (size_t)O * Hd + O;
+  const double *W1 = prm, *b1 = W1 + (size_t)Hd * F, *W2 = b1 + Hd, *b2 = W2 + (size_t)Hd * Hd;
+  const double *W3 = b2 + Hd, *b3 = W3 + (size_t)O * Hd;
+  double *gW1 = grad, *gb1 = gW1 + (size_t)Hd * F, *gW2 = gb1 + Hd, *gb2 = gW2 + (size_t)Hd * Hd;
+  double *gW3 = gb2 + Hd, *gb3 = gW3 + (size_t)O * Hd;
+  for (size_t i = 0; i < P; ++i) grad[i] = 0.0;
+  double *x = (double *)malloc(sizeof(double) * (size_t)F);
+  double *a1 = (double *)malloc(sizeof(double) * (size_t)Hd), *h1 = (double *)malloc(sizeof(double) * (size_t)Hd);
+  double *a2 = (double *)malloc(sizeof(double) * (size_t)Hd), *h2 = (double *)malloc(sizeof(double) * (size_t)Hd);
+  double *y = (double *)malloc(sizeof(double) * (size_t)O), *dy = (double *)malloc(sizeof(double) * (size_t)O);
+  double *dh2 = (double *)malloc(sizeof(double) * (size_t)Hd), *dh1 = (double *)malloc(sizeof(double) * (size_t)Hd);
+  double L = 0.0;
+  for (long long b = 0; b < B; ++b) {
+    mlp_normalise(f + (size_t)b * F, d, nref, x);
+    for (int i = 0; i < Hd; ++i) {
+      double s = b1[i];
+      for (int j = 0; j < F; ++j) s += W1[(size_t)i * F + j] * x[j];
+      a1[i] = s;
+      h1[i] = s > 0.0 ? s : 0.0;
+    }
+    for (int i = 0; i < Hd; ++i) {
+      double s = b2[i];
+      for (int j = 0; j < Hd; ++j) s += W2[(size_t)i * Hd + j] * h1[j];
+      a2[i] = s;
+      h2[i] = s > 0.0 ? s : 0.0;
+    }
+    for (int i = 0; i < O; ++i) {
+      double s = b3[i];
+      for (int j = 0; j < Hd; ++j) s += W3[(size_t)i * Hd + j] * h2[j];
+      y[i] = s;
+    }
+    const double *tb = t + (size_t)b * O;
+    for (int i = 0; i < O; ++i) {
+      double e = y[i] - tb[i];
+      double wgt = i < d ? 1.0 / d : 1.0;
+      L += wgt * e * e;
+      dy[i] = 2.0 * wgt * e / (double)B;
+    }
+    for (int j = 0; j < Hd; ++j) dh2[j] = 0.0;
+    for (int i = 0; i < O; ++i) {
+      gb3[i] += dy[i];
+      for (int j = 0; j < Hd; ++j) {
+        gW3[(size_t)i * Hd + j] += dy[i] * h2[j];
+        dh2[j] += W3[(size_t)i * Hd + j] * dy[i];
+      }
+    }
+    for (int j = 0; j < Hd; ++j) dh1[j] = 0.0;
+    for (int i = 0; i < Hd; ++i) {
+      double da = a2[i] > 0.0 ? dh2[i] : 0.0;
+      gb2[i] += da;
+      for (int j = 0; j < Hd; ++j) {
+        gW2[(size_t)i * Hd + j] += da * h1[j];
+        dh1[j] += W2[(size_t)i * Hd + j] * da;
+      }
+    }
+    for (int i = 0; i < Hd; ++i) {
+      double da = a1[i] > 0.0 ? dh1[i] : 0.0;
+      gb1[i] += da;
+      for (int j = 0; j < F; ++j) gW1[(size_t)i * F + j] += da * x[j];
+    }
+  }
+  free(x); free(a1); free(h1); free(a2); free(h2); free(y); free(dy); free(dh2); free(dh1);
+  return L / (double)B;
+}
