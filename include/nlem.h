@@ -212,6 +212,69 @@ int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch
  */
 int nlem_device_status(nlem_ctx* ctx);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper, which starts from the noisy or the NLM patch and
+ * uses one penalty mu for all problems): a 3-layer MLP with FP16 weights and FP32 arithmetic,
+ * 2d+2 inputs -> 128 -> 128 -> d+1 outputs (ReLU between layers), maps a problem's features
+ *   f = [m (d): weighted mean sum p_k a_k, q (d): coordinate-wise lower weighted median,
+ *        H = -sum p_k ln p_k, pmax = max p_k],  p_k = w_k / sum w,
+ * (inputs normalised as (v - 127.5)/64 for m and q, H / ln(nref), pmax as is) to
+ *   x0 = P_C(m + 16 * y[0:d]),  rho = exp(clamp(y[d], -12, 4)).
+ * Trained on solves the method itself produces (nlem_denoise_ex gives the labels) with the
+ * library's own forward, backward and Adam kernels.  Parameter vector layout (row-major):
+ *   W1 [128][2d+2], b1 [128], W2 [128][128], b2 [128], W3 [d+1][128], b3 [d+1].
+ * ------------------------------------------------------------------------------------------ */
+typedef struct nlem_warmstart nlem_warmstart;
+
+/* Number of parameters of the model for dimension d (-1 if d < 1). */
+long long nlem_ws_num_params(int d);
+/* New model for dimension d (1..81) with seeded He-normal weights on the context's device;
+ * nref normalises the entropy input (use the largest window size n, e.g. 441). */
+int nlem_ws_create(nlem_ctx* ctx, int d, float nref, unsigned long long seed, nlem_warmstart** ws);
+int nlem_ws_destroy(nlem_warmstart* ws);
+/* FP32 master parameters to / from host memory (set also resets the Adam state). */
+int nlem_ws_get_params(nlem_warmstart* ws, float* host_params);
+int nlem_ws_set_params(nlem_warmstart* ws, const float* host_params);
+/* Binary checkpoint: "NLEMWS01", d, hidden, nref, Adam step, parameters, Adam moments. */
+int nlem_ws_save(nlem_warmstart* ws, const char* path);
+int nlem_ws_load(nlem_warmstart* ws, const char* path);
+/* y [B][d+1] = network(feats [B][2d+2]) (device arrays). */
+int nlem_ws_forward(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, float* y, void* stream);
+/* Loss L = (1/B) sum_b [(1/d) sum_{c<d} (y_bc - t_bc)^2 + (y_bd - t_bd)^2] of a batch and its
+ * gradient with respect to the FP32 parameters (forward with the FP16 weights).
+ * loss: device float or NULL; grad: device [num_params] or NULL (kept inside ws). */
+int nlem_ws_loss_grad(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long B,
+                      float* loss, float* grad, void* stream);
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the loss of the batch. */
+int nlem_ws_train_step(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long B,
+                       float lr, float* loss, void* stream);
+/* y = network(feats), then x0 [B][d] and rho [B] as above (device arrays). */
+int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, nlem_box box, float* y,
+                    float* x0, float* rho, void* stream);
+
+/* Features f (above) of the NLEM problems of the listed pixels (device linear indices, NULL =
+ * all H*W in row-major order) into feats [npix or H*W][2d+2].  window^2 <= 512. */
+int nlem_features(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                  const int* pixels, long long npix, float* feats, void* stream);
+
+/* nlem_denoise on the listed pixels only (NULL = all), optionally from per-pixel start points
+ * x0 [pixel][d] and penalties rho_pix [pixel] (device, indexed by linear pixel), writing the
+ * centre pixel to out[pixel] and optionally the whole solution patch to z_out [pixel][d]. */
+int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                    float rho, int iters, nlem_box box, const nlem_options* opt, const int* pixels, long long npix,
+                    const float* x0, const float* rho_pix, float* out, int* iters_used, float* residual,
+                    float* z_out, void* stream);
+
+/* NLEM with the learned warm start: features -> network -> EM-ADMM from (x0, rho) with the
+ * stopping rule of opt (opt->tol > 0 required) and the cap iters; every pixel that reaches
+ * the cap is solved again by plain EM-ADMM (weighted-mean start, penalty rho_fallback).
+ * iters_used (required) holds the iterations of the solve that produced out.
+ * fallback_count (host, nullable): if given, the call waits and reports how many pixels fell
+ * back.  Workspace for the features and predictions is held by the context. */
+int nlem_denoise_warm(nlem_ctx* ctx, nlem_warmstart* ws, const float* image, int H, int W, int pitch, int patch,
+                      int window, float h, float rho_fallback, int iters, nlem_box box, const nlem_options* opt,
+                      float* out, int* iters_used, long long* fallback_count, void* stream);
+
 /*
  * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an
  * FMA as 2 flops), from a register-only FMA-chain kernel timed with CUDA events; also

@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     PREC_BF16,
     PREC_FP32,
     Context,
+    WarmStart,
     NlemError,
     em_solve,
     em_solve_batch,
@@ -27,7 +28,10 @@ from ._binding import (  # noqa: F401
     nlem_denoise,
     nlem_denoise_batch,
     nlem_denoise_batch_noalloc,
+    nlem_denoise_ex,
     nlem_denoise_host,
     nlem_device_status,
+    nlem_denoise_warm,
+    nlem_features,
     nlem_fp32_peak,
 )

@@ -73,11 +73,31 @@ def load_library():
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
         lib.nlem_device_status.argtypes = [vp]
         lib.nlem_bf16_weights.argtypes = [vp, vp, i, i, i, i, i, f, vp, vp]
+        lib.nlem_ws_num_params.argtypes = [i]
+        lib.nlem_ws_num_params.restype = ll
+        lib.nlem_ws_create.argtypes = [vp, i, f, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+        lib.nlem_ws_destroy.argtypes = [vp]
+        lib.nlem_ws_get_params.argtypes = [vp, vp]
+        lib.nlem_ws_set_params.argtypes = [vp, vp]
+        lib.nlem_ws_save.argtypes = [vp, ctypes.c_char_p]
+        lib.nlem_ws_load.argtypes = [vp, ctypes.c_char_p]
+        lib.nlem_ws_forward.argtypes = [vp, vp, vp, ll, vp, vp]
+        lib.nlem_ws_loss_grad.argtypes = [vp, vp, vp, vp, ll, vp, vp, vp]
+        lib.nlem_ws_train_step.argtypes = [vp, vp, vp, vp, ll, f, vp, vp]
+        lib.nlem_ws_predict.argtypes = [vp, vp, vp, ll, _Box, vp, vp, vp, vp]
+        lib.nlem_features.argtypes = [vp, vp, i, i, i, i, i, f, vp, ll, vp, vp]
+        lib.nlem_denoise_ex.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, ll, vp, vp,
+                                        vp, vp, vp, vp, vp]
+        lib.nlem_denoise_warm.argtypes = [vp, vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp,
+                                          ctypes.POINTER(ll), vp]
         lib.nlem_denoise_batch_noalloc.argtypes = [ctypes.POINTER(_ImageDesc), i, f, i, _Box,
                                                    ctypes.POINTER(_Options), vp]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
                      "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc",
-                     "nlem_device_status", "nlem_bf16_weights"):
+                     "nlem_device_status", "nlem_bf16_weights", "nlem_ws_create", "nlem_ws_destroy",
+                     "nlem_ws_get_params", "nlem_ws_set_params", "nlem_ws_save", "nlem_ws_load", "nlem_ws_forward",
+                     "nlem_ws_loss_grad", "nlem_ws_train_step", "nlem_ws_predict", "nlem_features", "nlem_denoise_ex",
+                     "nlem_denoise_warm"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -369,3 +389,154 @@ def nlem_bf16_weights(image, patch=9, window=21, h=300.0, ctx: Context | None = 
     _check(load_library().nlem_bf16_weights(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
                                             _ptr(out), _stream(image.device)))
     return out
+
+
+class WarmStart:
+    """Learned warm-start model (include/nlem.h: nlem_ws_*) on the context's device."""
+
+    def __init__(self, d, nref=441.0, seed=1, ctx: Context | None = None):
+        import torch
+        self.ctx = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+        self.d = int(d)
+        h = ctypes.c_void_p()
+        _check(load_library().nlem_ws_create(self.ctx.handle, self.d, float(nref), int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.num_params = int(load_library().nlem_ws_num_params(self.d))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().nlem_ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(load_library().nlem_ws_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters")
+        _check(load_library().nlem_ws_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def save(self, path):
+        _check(load_library().nlem_ws_save(self.handle, str(path).encode()))
+
+    def load(self, path):
+        _check(load_library().nlem_ws_load(self.handle, str(path).encode()))
+
+    def forward(self, feats):
+        import torch
+        B = feats.shape[0]
+        y = torch.empty((B, self.d + 1), dtype=torch.float32, device=feats.device)
+        _check(load_library().nlem_ws_forward(self.ctx.handle, self.handle, _ptr(feats), B, _ptr(y),
+                                              _stream(feats.device)))
+        return y
+
+    def loss_grad(self, feats, targets):
+        import torch
+        B = feats.shape[0]
+        loss = torch.zeros(1, dtype=torch.float32, device=feats.device)
+        grad = torch.empty(self.num_params, dtype=torch.float32, device=feats.device)
+        _check(load_library().nlem_ws_loss_grad(self.ctx.handle, self.handle, _ptr(feats), _ptr(targets), B,
+                                                _ptr(loss), _ptr(grad), _stream(feats.device)))
+        return loss, grad
+
+    def train_step(self, feats, targets, lr, loss=None):
+        B = feats.shape[0]
+        _check(load_library().nlem_ws_train_step(self.ctx.handle, self.handle, _ptr(feats), _ptr(targets), B,
+                                                 float(lr), _ptr(loss), _stream(feats.device)))
+
+    def predict(self, feats, box=(0.0, 255.0)):
+        import torch
+        B = feats.shape[0]
+        dev = feats.device
+        y = torch.empty((B, self.d + 1), dtype=torch.float32, device=dev)
+        x0 = torch.empty((B, self.d), dtype=torch.float32, device=dev)
+        rho = torch.empty(B, dtype=torch.float32, device=dev)
+        _check(load_library().nlem_ws_predict(self.ctx.handle, self.handle, _ptr(feats), B, _Box(*box), _ptr(y),
+                                              _ptr(x0), _ptr(rho), _stream(dev)))
+        return y, x0, rho
+
+
+def nlem_features(image, patch=7, window=21, h=200.0, pixels=None, ctx: Context | None = None):
+    """Warm-start features [npix, 2d+2] of the listed pixels' NLEM problems (all if None)."""
+    import torch
+    H, W = image.shape
+    c = ctx or _ctx(image.device)
+    n = pixels.numel() if pixels is not None else H * W
+    d = patch * patch
+    feats = torch.empty((n, 2 * d + 2), dtype=torch.float32, device=image.device)
+    if pixels is not None:
+        _need(pixels, torch.int32, (n,), "pixels")
+    _check(load_library().nlem_features(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+                                        _ptr(pixels), n, _ptr(feats), _stream(image.device)))
+    return feats
+
+
+def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
+                    init=INIT_WEIGHTED_MEAN, pixels=None, x0=None, rho_pix=None, z_out=False, ctx: Context | None = None,
+                    out=None):
+    """NLEM on a pixel list with optional per-pixel start points / penalties (indexed by
+    linear pixel) and the full solution patches.  Returns dict(out, iters_used, residual[, z])."""
+    import torch
+    H, W = image.shape
+    c = ctx or _ctx(image.device)
+    dev = image.device
+    d = patch * patch
+    res = out or {}
+    o = res.get("out")
+    if o is None:
+        o = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.zeros((H, W), dtype=torch.int32, device=dev)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    z = None
+    if z_out:
+        z = res.get("z")
+        if z is None:
+            z = torch.zeros((H * W, d), dtype=torch.float32, device=dev)
+    n = pixels.numel() if pixels is not None else 0
+    opts = _options(tol, check_every, PREC_FP32, init)
+    _check(load_library().nlem_denoise_ex(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h), float(rho),
+                                          int(iters), _Box(*box), ctypes.byref(opts), _ptr(pixels), n, _ptr(x0),
+                                          _ptr(rho_pix), _ptr(o), _ptr(used), _ptr(resid), _ptr(z), _stream(dev)))
+    r = dict(out=o, iters_used=used, residual=resid)
+    if z_out:
+        r["z"] = z
+    return r
+
+
+def nlem_denoise_warm(ws: WarmStart, image, patch=7, window=21, h=200.0, rho_fallback=1.0, iters=300,
+                      box=(0.0, 255.0), tol=1e-4, check_every=10, count_fallback=True, ctx: Context | None = None,
+                      out=None):
+    """NLEM with the learned warm start and plain-ADMM fallback.  Returns dict(out,
+    iters_used, fallback) (fallback = pixels solved again, or None if not counted)."""
+    import torch
+    H, W = image.shape
+    c = ctx or ws.ctx
+    dev = image.device
+    res = out or {}
+    o = res.get("out")
+    if o is None:
+        o = torch.empty((H, W), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty((H, W), dtype=torch.int32, device=dev)
+    opts = _options(tol, check_every, PREC_FP32, INIT_WEIGHTED_MEAN)
+    fb = ctypes.c_longlong(-1)
+    _check(load_library().nlem_denoise_warm(c.handle, ws.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+                                            float(rho_fallback), int(iters), _Box(*box), ctypes.byref(opts), _ptr(o),
+                                            _ptr(used), ctypes.byref(fb) if count_fallback else None, _stream(dev)))
+    return dict(out=o, iters_used=used, fallback=int(fb.value) if count_fallback else None)

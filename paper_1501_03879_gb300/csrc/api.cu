@@ -16,40 +16,7 @@
 #include "batch.h"
 #include "kernels.h"
 
-// A captured batch: the descriptors and parameters it was built for, the launch shape and the
-// instantiated graph (queue reset + persistent launch), which reads the workspace below.
-struct BatchPlan {
-  std::vector<nlemk::BatchImage> imgs;
-  nlemk::SolveParams prm{};
-  int init_mode = 0;
-  nlemk::BatchConfig cfg{};
-  long long total = 0;
-  cudaGraphExec_t exec = nullptr;
-};
-
-struct nlem_ctx {
-  int device = 0;
-  int sm_count = 0;
-  // workspace for the host-buffer entry point (grown on demand, freed by destroy)
-  float* ws_img = nullptr;
-  float* ws_out = nullptr;
-  int* ws_iters = nullptr;
-  size_t ws_pixels = 0;
-  // workspace of the mixed-precision path: weight table [pixel][window index] and the flag the
-  // tensor-core kernel raises if one of its bounded waits runs out
-  float* ws_wtab = nullptr;
-  size_t ws_wtab_floats = 0;
-  int* ws_err = nullptr;
-  // workspace of the batched launch: image descriptors and the work-queue counter
-  nlemk::BatchImage* ws_batch = nullptr;
-  int ws_batch_cap = 0;
-  unsigned long long* ws_queue = nullptr;
-  cudaStream_t cap_stream = nullptr;                // private stream used for graph capture
-  std::map<std::string, nlemk::BatchConfig> tune;   // autotuner results by workload class
-  BatchPlan plan;
-  bool have_plan = false;
-  std::string last_cfg;
-};
+#include "ctx.h"
 
 namespace {
 
@@ -161,6 +128,12 @@ int nlem_ctx_destroy(nlem_ctx* ctx) {
   cudaFree(ctx->ws_queue);
   cudaFree(ctx->ws_wtab);
   cudaFree(ctx->ws_err);
+  cudaFree(ctx->ws_feats);
+  cudaFree(ctx->ws_y);
+  cudaFree(ctx->ws_x0);
+  cudaFree(ctx->ws_rho);
+  cudaFree(ctx->ws_list);
+  cudaFree(ctx->ws_count);
   delete ctx;
   return NLEM_OK;
 }
@@ -248,6 +221,10 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   L.sm_count = ctx->sm_count;
   L.stream = (cudaStream_t)stream;
   L.wtab = nullptr;
+  L.pix_list = nullptr;
+  L.n_list = nullptr;
+  L.max_items = 0;
+  L.ex = nlemk::PixelExtra{};
   if (opt && opt->precision == NLEM_PREC_BF16) {
     // cross terms on the tensor cores into the weight table, then the solver reads it
     const size_t need = (size_t)H * W * (size_t)window * window;

@@ -46,10 +46,10 @@ nlem_batch_kernel(const BatchImage* __restrict__ imgs, int count, long long tota
       const long long pix = item - im.pix_begin;
       if (im.patch == KA) {
         nlem_pixel<CA, KA>(smA, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
-                           im.iters, im.resid, nullptr, nullptr);
+                           im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
       } else {
         nlem_pixel<CB, KB>(smB, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
-                           im.iters, im.resid, nullptr, nullptr);
+                           im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
       }
     }
   }

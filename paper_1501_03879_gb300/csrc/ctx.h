@@ -1,0 +1,54 @@
+// Context object behind the nlem_ctx handle of the C ABI (shared by the host-side units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+
+// A captured batch: the descriptors and parameters it was built for, the launch shape and the
+// instantiated graph (queue reset + persistent launch), which reads the workspace below.
+struct BatchPlan {
+  std::vector<nlemk::BatchImage> imgs;
+  nlemk::SolveParams prm{};
+  int init_mode = 0;
+  nlemk::BatchConfig cfg{};
+  long long total = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct nlem_ctx {
+  int device = 0;
+  int sm_count = 0;
+  // workspace for the host-buffer entry point (grown on demand, freed by destroy)
+  float* ws_img = nullptr;
+  float* ws_out = nullptr;
+  int* ws_iters = nullptr;
+  size_t ws_pixels = 0;
+  // workspace of the mixed-precision path: weight table [pixel][window index] and the flag the
+  // tensor-core kernel raises if one of its bounded waits runs out
+  float* ws_wtab = nullptr;
+  size_t ws_wtab_floats = 0;
+  int* ws_err = nullptr;
+  // workspace of the batched launch: image descriptors and the work-queue counter
+  nlemk::BatchImage* ws_batch = nullptr;
+  int ws_batch_cap = 0;
+  unsigned long long* ws_queue = nullptr;
+  cudaStream_t cap_stream = nullptr;                // private stream used for graph capture
+  std::map<std::string, nlemk::BatchConfig> tune;   // autotuner results by workload class
+  BatchPlan plan;
+  bool have_plan = false;
+  std::string last_cfg;
+  // workspace of the warm-started and pixel-list entry points
+  float* ws_feats = nullptr;
+  float* ws_y = nullptr;
+  float* ws_x0 = nullptr;
+  float* ws_rho = nullptr;
+  int* ws_list = nullptr;
+  long long* ws_count = nullptr;   // device element counts: [0] fallback list, [1] caller list
+  size_t ws_warm_pixels = 0;
+  int ws_warm_d = 0;
+};
+

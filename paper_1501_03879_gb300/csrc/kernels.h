@@ -22,6 +22,14 @@ struct EmLaunch {
   cudaStream_t stream;
 };
 
+// Optional per-pixel inputs and outputs of the NLEM kernel (all NULL = plain NLEM).
+struct PixelExtra {
+  const float* x0;      // [pixel][d] start points (projected onto C), or NULL
+  const float* rho;     // [pixel] penalties, or NULL for the launch's rho
+  float* z_out;         // [pixel][d] full solution patch, or NULL
+  float* feats;         // [pixel][2d+2] warm-start features; when set, no solve is run
+};
+
 struct NlemLaunch {
   const float* img;
   int H, W, pitch, patch, S;
@@ -35,6 +43,10 @@ struct NlemLaunch {
   double* obj64;
   double* kkt64;
   const float* wtab;     // precomputed weights [pixel][window index] or NULL
+  const int* pix_list;   // process only these pixels (count in *n_list), or NULL for all
+  const long long* n_list;
+  long long max_items;   // upper bound of *n_list (sizes the grid)
+  PixelExtra ex;
   int sm_count;
   cudaStream_t stream;
 };

@@ -116,13 +116,144 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
 // reflect-padded image around the clipped search window -> patch rows in shared memory ->
 // weights exp(-||P_i-P_j||^2/h^2) -> start point -> EM-ADMM -> centre coordinate.
 // Ends with a barrier, so the caller may start the next pixel at once.
+// Warm-start features of one NLEM problem from the points and weights set up in shared
+// memory (lam holds the weights themselves): [m (d), q (d), H, pmax] with p = w / sum w,
+// m = sum p a (not projected), q = coordinate-wise lower weighted median (bitonic sort of each
+// coordinate's values, cumulative weights in FP64), H = -sum p ln p, pmax = max p.
+// sortbuf: 8 * 512 keys then 8 * 512 weights (dynamic shared memory past the solver's carve).
+constexpr int kSortCoords = 8, kSortLen = 512;
+
+template <class C>
+__device__ void features_body(Smem<C>& sm, const float (&wreg)[C::P], int n, float* __restrict__ fout,
+                              float* __restrict__ sortbuf) {
+  const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
+  const bool last = (g == C::G - 1);
+  __shared__ unsigned int s_wmax;
+  __shared__ float s_W, s_WlnW;
+  if (t == 0) s_wmax = 0u;
+  __syncthreads();
+  float acc[C::QR];
+#pragma unroll
+  for (int i = 0; i < C::QR; ++i) acc[i] = 0.f;
+#pragma unroll
+  for (int p = 0; p < C::P; ++p) {
+    const int j = pg + p * C::NG;
+    float a[C::Q];
+    load_slice<C>(sm.pts + j * C::DP + g * C::QA, last, a);
+    const float w = wreg[p];
+#pragma unroll
+    for (int q = 0; q < C::Q; ++q) acc[q] = fmaf(w, a[q], acc[q]);
+    if (g == 0) {
+      acc[C::Q] += w;
+      acc[C::Q + 1] += w > 0.f ? w * logf(w) : 0.f;
+      atomicMax(&s_wmax, __float_as_uint(w));   // w >= 0: integer order is float order
+    }
+  }
+  float4 t0, t1;
+  block_reduce<C>(sm, acc, t0, t1);
+  if (warp == 0) {
+    constexpr int cq = C::Q / 4;
+    float vW = lane == cq ? f4get(t0, C::Q - 4 * cq) : 0.f;
+    float vL = 0.f;
+    {
+      const int col1 = (C::Q + 1) / 4;
+      const int sl1 = (C::Q + 1) - 4 * col1;
+      if (lane == col1) vL = f4get(t0, sl1);
+    }
+    vW = warp_sum(vW);
+    vL = warp_sum(vL);
+    if (lane == 0) {
+      s_W = vW;
+      s_WlnW = vL;
+    }
+    __syncwarp();
+    const float inv = 1.f / vW;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int col = lane + 32 * h2;
+      if (col >= C::COLS) continue;
+      const float4 tv = h2 == 0 ? t0 : t1;
+      const int sg = col / C::NQR, quad = col - sg * C::NQR;
+      const int real = slice_real<C>(sg, C::D);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int slot = 4 * quad + i;
+        if (slot < real) fout[sg * C::Q + slot] = f4get(tv, i) * inv;
+      }
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    const float W = s_W;
+    fout[2 * C::D] = logf(W) - s_WlnW / W;
+    fout[2 * C::D + 1] = __uint_as_float(s_wmax) / W;
+  }
+  float* keys = sortbuf;
+  float* vals = sortbuf + kSortCoords * kSortLen;
+  for (int c0 = 0; c0 < C::D; c0 += kSortCoords) {
+    for (int idx = t; idx < kSortCoords * kSortLen; idx += C::NT) {
+      const int cc = idx / kSortLen, j = idx - cc * kSortLen, c = c0 + cc;
+      float k = __int_as_float(0x7f800000), v = 0.f;   // padding: +inf with weight 0
+      if (c < C::D && j < n) {
+        k = sm.pts[j * C::DP + (c / C::Q) * C::QA + (c % C::Q)];
+        v = sm.lam[j];
+      }
+      keys[idx] = k;
+      vals[idx] = v;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= kSortLen; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int pidx = t; pidx < kSortCoords * (kSortLen / 2); pidx += C::NT) {
+          const int cc = pidx / (kSortLen / 2), pi = pidx - cc * (kSortLen / 2);
+          const int i = (pi / jj) * 2 * jj + (pi % jj), partner = i + jj;
+          const bool asc = (i & kk) == 0;
+          float* kb = keys + cc * kSortLen;
+          float* vb = vals + cc * kSortLen;
+          const float a = kb[i], b = kb[partner];
+          if ((a > b) == asc && a != b) {
+            kb[i] = b;
+            kb[partner] = a;
+            const float va = vb[i];
+            vb[i] = vb[partner];
+            vb[partner] = va;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (t < kSortCoords && c0 + t < C::D) {
+      const float* kb = keys + t * kSortLen;
+      const float* vb = vals + t * kSortLen;
+      double tot = 0.0;
+      for (int j = 0; j < n; ++j) tot += (double)vb[j];
+      double cum = 0.0;
+      float med = kb[n - 1];
+      for (int j = 0; j < n; ++j) {
+        cum += (double)vb[j];
+        if (cum >= 0.5 * tot) {
+          med = kb[j];
+          break;
+        }
+      }
+      fout[C::D + c0 + t] = med;
+    }
+    __syncthreads();
+  }
+}
+
 template <class C, int K>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
                            double* __restrict__ obj64, double* __restrict__ kkt64,
-                           const float* __restrict__ wtab = nullptr) {
+                           const float* __restrict__ wtab, const PixelExtra& ex, long long item = -1) {
   static_assert(K * K == C::D, "patch size must match the compiled dimension");
+  SolveParams pp = prm;   // the pixel's own penalty when the caller passes one
+  if (ex.rho) {
+    pp.mu = ex.rho[pix];
+    pp.inv_mu = 1.f / pp.mu;
+  }
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
   const bool last = (g == C::G - 1);
   constexpr int HK = (K - 1) / 2;
@@ -186,12 +317,31 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
       float w = j < n ? expf(-Dp * inv_h2) : 0.f;
       if (wtab) w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;   // precomputed (BF16 mode)
       wreg[p] = w;
-      if (g == 0) sm.lam[j] = w * prm.inv_mu;
+      if (g == 0) sm.lam[j] = w * pp.inv_mu;
     }
   }
-  if (init_mode == 1) {
+  if (ex.feats) {   // features only: no solve
+    __syncthreads();
+    extern __shared__ float4 smem_raw[];
+    // feature rows follow the pixel list (row = item), or the image when there is no list
+    features_body<C>(sm, wreg, n, ex.feats + (item >= 0 ? item : pix) * (long long)(2 * C::D + 2),
+                     reinterpret_cast<float*>(smem_raw) + C::TOTAL);
+    return;
+  }
+  if (ex.x0) {   // caller's start point, projected onto C
     for (int i = t; i < C::VEC; i += C::NT) {
-      const float z = clampf(sm.pcv[i], prm.lo, prm.hi);
+      const int sg = i / C::QA, slot = i - sg * C::QA;
+      const float zz = slot < slice_real<C>(sg, C::D)
+                           ? clampf(__ldg(ex.x0 + pix * (long long)C::D + sg * C::Q + slot), pp.lo, pp.hi)
+                           : 0.f;
+      sm.zv[i] = zz;
+      sm.cv[i] = zz;
+      sm.sgv[i] = 0.f;
+    }
+    __syncthreads();
+  } else if (init_mode == 1) {
+    for (int i = t; i < C::VEC; i += C::NT) {
+      const float z = clampf(sm.pcv[i], pp.lo, pp.hi);
       const int sg = i / C::QA, slot = i - sg * C::QA;
       const float zz = slot < slice_real<C>(sg, C::D) ? z : 0.f;
       sm.zv[i] = zz;
@@ -201,9 +351,13 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
     __syncthreads();
   } else {
     __syncthreads();   // lam visible, tile no longer needed (wred aliases it)
-    weighted_mean_start<C>(sm, wreg, n, C::D, prm);
+    weighted_mean_start<C>(sm, wreg, n, C::D, pp);
   }
-  admm_iterate<C>(sm, n, C::D, prm);
+  admm_iterate<C>(sm, n, C::D, pp);
+  if (ex.z_out) {
+    for (int q = t; q < C::D; q += C::NT)
+      ex.z_out[pix * (long long)C::D + q] = sm.zv[(q / C::Q) * C::QA + (q % C::Q)];
+  }
   if (t == 0) {
     constexpr int qc = (C::D - 1) / 2;
     constexpr int sg = qc / C::Q, slot = qc - sg * C::Q;
@@ -222,7 +376,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
       }
       return exp(-D * ih2);
     };
-    fp64_check<C>(sm, n, C::D, prm, wfun, F, Rk);
+    fp64_check<C>(sm, n, C::D, pp, wfun, F, Rk);
     if (t == 0) {
       if (obj64) obj64[pix] = F;
       if (kkt64) kkt64[pix] = Rk;
@@ -236,13 +390,16 @@ __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
             float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64,
-            const float* __restrict__ wtab) {
+            const float* __restrict__ wtab, const int* __restrict__ pix_list,
+            const long long* __restrict__ n_list, PixelExtra ex) {
   extern __shared__ float4 smem_raw[];
   Smem<C> sm(reinterpret_cast<float*>(smem_raw));
-  const long long npix = (long long)H * W;
-  for (long long pix = blockIdx.x; pix < npix; pix += gridDim.x)
+  const long long items = pix_list ? *n_list : (long long)H * W;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const long long pix = pix_list ? (long long)pix_list[it] : it;
     nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
-                     wtab);
+                     wtab, ex, it);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -266,16 +423,19 @@ template <class C, int K>
 inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
   if ((L.S + K - 1) * (L.S + K - 1) > C::SZ_WRED) return -1;   // tile must fit its region
   auto kern = nlem_kernel<C, K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+  // the features mode sorts in shared memory past the solver's carve
+  const size_t smem = C::SMEM_BYTES + (L.ex.feats ? (size_t)2 * kSortCoords * kSortLen * sizeof(float) : 0);
+  if (smem > 232448) return -1;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  long long npix = (long long)L.H * L.W;
+  long long npix = L.pix_list ? L.max_items : (long long)L.H * L.W;
   long long grid = npix;
   long long cap = (long long)L.sm_count * C::MIN_BLOCKS * grid_mult;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.img, L.H, L.W, L.pitch, L.S, L.inv_h2, L.inv_h2_exact, L.prm,
-                                                          L.init_mode, L.out, L.iters_used, L.resid, L.obj64,
-                                                          L.kkt64, L.wtab);
+  kern<<<(unsigned)grid, C::NT, smem, L.stream>>>(L.img, L.H, L.W, L.pitch, L.S, L.inv_h2, L.inv_h2_exact, L.prm,
+                                                 L.init_mode, L.out, L.iters_used, L.resid, L.obj64, L.kkt64, L.wtab,
+                                                 L.pix_list, L.n_list, L.ex);
   return (int)cudaGetLastError();
 }
 

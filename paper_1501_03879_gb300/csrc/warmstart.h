@@ -1,0 +1,42 @@
+// Internal interface of the learned warm start (model state and its device kernels).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace nlemk {
+
+constexpr int kWsHidden = 128;
+constexpr float kDeltaScale = 16.f;    // x0 = P_C(m + kDeltaScale * y[0:d])
+constexpr float kLogRhoMin = -12.f;    // rho = exp(clamp(y[d], kLogRhoMin, kLogRhoMax))
+constexpr float kLogRhoMax = 4.f;
+
+struct WsModel {
+  int d = 0;
+  float nref = 441.f;       // entropy normaliser: H / log(nref)
+  long long step = 0;       // Adam steps taken
+  float* p32 = nullptr;     // FP32 master parameters
+  __half* w16 = nullptr;    // FP16 copy read by the forward pass
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+};
+
+// Activations and gradients of one training batch (grown on demand).
+struct WsScratch {
+  long long cap = 0;
+  float *y = nullptr, *xs = nullptr, *a1 = nullptr, *a2 = nullptr, *dy = nullptr, *da1 = nullptr, *da2 = nullptr;
+  float* grad = nullptr;
+};
+
+long long ws_num_params(int d);
+int ws_forward(const WsModel& m, const float* feats, long long B, float* y, float* xs, float* a1s, float* a2s,
+               int sm_count, cudaStream_t s);
+int ws_loss_grad(const WsModel& m, WsScratch& sc, const float* feats, const float* tgt, long long B, float* loss,
+                 float* grad, int sm_count, cudaStream_t s);
+int ws_adam(WsModel& m, const float* grad, float lr, int sm_count, cudaStream_t s);
+int ws_sync_half(WsModel& m, int sm_count, cudaStream_t s);
+int ws_apply(const float* feats, const float* y, long long B, int d, float lo, float hi, float* x0, float* rho,
+             int sm_count, cudaStream_t s);
+int ws_fallback_list(const int* iters_used, long long npix, int cap, int* list, long long* count, int sm_count,
+                     cudaStream_t s);
+
+}  // namespace nlemk

@@ -1,0 +1,102 @@
+"""Training of the learned warm start from solves the method itself produces.
+
+For each training image, a seeded sample of pixels is solved (nlem_denoise_ex, tolerance
+1e-4) from the weighted-mean start with every penalty of a grid; the label penalty is the one
+that reaches the tolerance in the fewest iterations, and the label start point is the solution
+patch of a tight solve (tolerance 1e-6) with that penalty.  Targets for the network output y:
+y[0:d] = (z* - m) / 16 and y[d] = ln rho*.  Training runs the library's forward, backward and
+Adam kernels on minibatches; torch is used only to hold device arrays and to shuffle indices.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _binding as B
+
+RHO_GRID = (1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0)
+DELTA_SCALE = 16.0
+
+
+def make_training_set(images, hs, patch=7, window=21, per_image=4096, seed=0, tol=1e-4, check_every=5, cap=300,
+                      tight_tol=1e-6, tight_cap=2000, rho_grid=RHO_GRID, ctx=None):
+    """images: float32 CUDA tensors [H, W]; hs: their weight scales h.  Returns (feats [N,2d+2],
+    targets [N,d+1], info) on the device."""
+    import torch
+    d = patch * patch
+    feats_all, tgt_all = [], []
+    rng = np.random.default_rng(seed)
+    best_counts = np.zeros(len(rho_grid), dtype=np.int64)
+    for img, h in zip(images, hs):
+        H, W = img.shape
+        dev = img.device
+        k = min(per_image, H * W)
+        pix_np = np.sort(rng.choice(H * W, k, replace=False)).astype(np.int32)
+        pix = torch.from_numpy(pix_np).to(dev)
+        feats = B.nlem_features(img, patch, window, h, pixels=pix, ctx=ctx)
+        best_it = torch.full((k,), 1 << 30, dtype=torch.int32, device=dev)
+        best_rho = torch.ones(k, dtype=torch.float32, device=dev)
+        pl = pix.long()
+        for rho in rho_grid:
+            r = B.nlem_denoise_ex(img, patch, window, h, rho=rho, iters=cap, tol=tol, check_every=check_every,
+                                  pixels=pix, ctx=ctx)
+            it = r["iters_used"].reshape(-1)[pl]
+            better = it < best_it
+            best_it = torch.where(better, it, best_it)
+            best_rho = torch.where(better, torch.full_like(best_rho, rho), best_rho)
+        for j, rho in enumerate(rho_grid):
+            best_counts[j] += int((best_rho == rho).sum().item())
+        rho_map = torch.ones(H * W, dtype=torch.float32, device=dev)
+        rho_map[pl] = best_rho
+        r = B.nlem_denoise_ex(img, patch, window, h, rho=1.0, iters=tight_cap, tol=tight_tol, check_every=check_every,
+                              pixels=pix, rho_pix=rho_map, z_out=True, ctx=ctx)
+        z = r["z"][pl]
+        tgt = torch.empty((k, d + 1), dtype=torch.float32, device=dev)
+        tgt[:, :d] = (z - feats[:, :d]) / DELTA_SCALE
+        tgt[:, d] = torch.log(best_rho)
+        feats_all.append(feats)
+        tgt_all.append(tgt)
+    info = {"rho_grid": list(rho_grid), "best_rho_counts": best_counts.tolist()}
+    return torch.cat(feats_all), torch.cat(tgt_all), info
+
+
+def train(ws: B.WarmStart, feats, targets, epochs=10, batch=4096, lr=1e-3, seed=0, log_every=0):
+    """Adam on minibatches of the training set; returns the mean loss of each epoch."""
+    import torch
+    N = feats.shape[0]
+    g = torch.Generator(device=feats.device)
+    g.manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=feats.device)
+    history = []
+    for ep in range(epochs):
+        perm = torch.randperm(N, generator=g, device=feats.device)
+        tot, nb = 0.0, 0
+        for s in range(0, N - batch + 1 if N >= batch else 1, batch):
+            idx = perm[s:s + batch]
+            f = feats[idx].contiguous()
+            t = targets[idx].contiguous()
+            ws.train_step(f, t, lr, loss=loss)
+            tot += float(loss.item()) if log_every else 0.0
+            nb += 1
+        if log_every:
+            history.append(tot / max(nb, 1))
+        else:
+            l, _ = ws.loss_grad(feats[:min(N, 16384)].contiguous(), targets[:min(N, 16384)].contiguous())
+            history.append(float(l.item()))
+    return history
+
+
+def evaluate(ws: B.WarmStart, image, h, patch=7, window=21, cap=300, tol=1e-4, check_every=10, rho_plain=1.0,
+             ctx=None):
+    """Warm-started vs plain EM-ADMM on one image: mean iterations to the tolerance and the
+    number of pixels that fell back."""
+    import torch
+    warm = B.nlem_denoise_warm(ws, image, patch, window, h, rho_fallback=rho_plain, iters=cap, tol=tol,
+                               check_every=check_every, ctx=ctx)
+    plain = B.nlem_denoise(image, patch, window, h, rho=rho_plain, iters=cap, tol=tol, check_every=check_every,
+                           ctx=ctx)
+    torch.cuda.synchronize()
+    return dict(warm_iters=float(warm["iters_used"].float().mean().item()),
+                plain_iters=float(plain["iters_used"].float().mean().item()),
+                fallback=warm["fallback"], warm=warm, plain=plain)
