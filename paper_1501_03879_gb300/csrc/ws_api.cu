@@ -318,7 +318,8 @@ int nlem_features(nlem_ctx* ctx, const float* image, int H, int W, int pitch, in
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (!feats) return wfail(NLEM_ERR_INVALID, "feats is NULL");
-  if (window * window > 512) return wfail(NLEM_ERR_UNSUPPORTED, "features need window^2 <= 512");
+  if ((window + patch - 1) * (window + patch - 1) > 1024)
+    return wfail(NLEM_ERR_UNSUPPORTED, "features need (window + patch - 1)^2 <= 1024");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   nlemk::NlemLaunch L = base_launch(ctx, image, H, W, pitch, patch, window, h, 1.f, 0, nlem_box{0.f, 255.f},
