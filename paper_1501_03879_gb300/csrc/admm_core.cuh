@@ -10,7 +10,8 @@
 //       e_k(t+1) = c(t) + h_k(t),   c(t) = 2 z(t) - z(t-1),   h_k(t) = g_k(t) - a_k,
 //   so the only per-point state is h_k (n*d floats), started at h_k = -a_k with
 //   z(-1) = z(0).  One iteration per element is then: e = c + h, ||e||^2 += e*e,
-//   sum_g += s*e, h = s*e - a: one FADD and three FFMA.
+//   sum_g += s*e, h = s*e - a: one FADD and three FFMA, issued as packed FP32 pairs
+//   (FADD2 / FFMA2) over consecutive slots, so each instruction serves two coordinates.
 //
 // Layout: G consecutive lanes share a point; lane g of a group owns coordinate slice
 // [g*Q, g*Q+Q) (the last slice may be shorter: phantom slots read as 0).  A lane owns P
@@ -187,11 +188,14 @@ __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     if (col < C::COLS) {
       const int g = col / C::NQR, quad = col - g * C::NQR;
+      float4 s1 = s;   // two partial sums halve the dependent-add chain
 #pragma unroll
-      for (int m = 0; m < PER; ++m) {
+      for (int m = 0; m < PER; m += 2) {
         const int l = g * LPG + part * PER + m;
         s = f4add(s, wbase[l * C::NQR + quad]);
+        if (m + 1 < PER) s1 = f4add(s1, wbase[(l + 1) * C::NQR + quad]);
       }
+      s = f4add(s, s1);
     }
 #pragma unroll
     for (int o = CP2; o < 32; o <<= 1) {
@@ -307,41 +311,58 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
   const float inv_n = 1.f / (float)n;
   const float fn = (float)n;
 
-  float h[C::P][C::Q];
+  // state h as coordinate pairs (packed FP32: one FADD2 / FFMA2 serves two slots) plus the
+  // single last slot when Q is odd
+  constexpr int NP2 = C::Q / 2;
+  float2 h2[C::P][NP2];
+  float h1[C::P];
 #pragma unroll
   for (int p = 0; p < C::P; ++p) {
     const int j = pg + p * C::NG;
     float a[C::Q];
     load_slice<C>(sm.pts + j * C::DP + g * C::QA, last, a);
 #pragma unroll
-    for (int q = 0; q < C::Q; ++q) h[p][q] = -a[q];
+    for (int k = 0; k < NP2; ++k) h2[p][k] = make_float2(-a[2 * k], -a[2 * k + 1]);
+    h1[p] = (C::Q % 2) ? -a[C::Q - 1] : 0.f;
   }
 
   int it = 0;
   float resid = 0.f;
   for (it = 1; it <= prm.iters; ++it) {
     const bool check = (it == prm.iters) || (prm.tol > 0.f && (it % prm.check_every) == 0);
-    // phase 1: e = c + h (in place) and squared norms, one float4 of c at a time
+    // phase 1: e = c + h (in place) and squared norms, one float4 of c at a time; the
+    // points are innermost so that consecutive FFMA2s feed different norm accumulators
     float s[C::P];
-#pragma unroll
-    for (int p = 0; p < C::P; ++p) s[p] = 0.f;
     {
+      float2 s2[C::P];
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) s2[p] = make_float2(0.f, 0.f);
       const float* crow = sm.cv + g * C::QA;
 #pragma unroll
       for (int i = 0; i < C::NQA; ++i) {
         const float4 c4 = load_quad<C>(crow, i, last);
 #pragma unroll
-        for (int p = 0; p < C::P; ++p) {
+        for (int jh = 0; jh < 2; ++jh) {
+          const int q0 = 4 * i + 2 * jh;
+          if (q0 + 1 < C::Q) {
+            const float2 c2 = jh == 0 ? make_float2(c4.x, c4.y) : make_float2(c4.z, c4.w);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int q = 4 * i + c;
-            if (q < C::Q) {
-              h[p][q] += f4get(c4, c);
-              s[p] = fmaf(h[p][q], h[p][q], s[p]);
+            for (int p = 0; p < C::P; ++p) {
+              h2[p][q0 / 2] = __fadd2_rn(h2[p][q0 / 2], c2);
+              s2[p] = __ffma2_rn(h2[p][q0 / 2], h2[p][q0 / 2], s2[p]);
+            }
+          } else if (q0 < C::Q) {
+            const float c1 = jh == 0 ? c4.x : c4.z;
+#pragma unroll
+            for (int p = 0; p < C::P; ++p) {
+              h1[p] += c1;
+              s2[p].x = fmaf(h1[p], h1[p], s2[p].x);
             }
           }
         }
       }
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) s[p] = s2[p].x + s2[p].y;
     }
 #pragma unroll
     for (int p = 0; p < C::P; ++p) s[p] = point_sum<C>(s[p]);
@@ -365,19 +386,27 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
       for (int p = 0; p < C::P; ++p) {
         const float* arow = sm.pts + (pg + p * C::NG) * C::DP + g * C::QA;
         const float oms = 1.f - s[p];
+        const float2 oms2 = make_float2(oms, oms);
+        float2 dd2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < C::NQA; ++i) {
           const float4 a4 = load_quad<C>(arow, i, last);
           const float4 c4 = load_quad<C>(crow, i, last);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int q = 4 * i + c;
-            if (q < C::Q) {
-              const float dq = fmaf(oms, h[p][q], f4get(a4, c) - f4get(c4, c));
+          for (int jh = 0; jh < 2; ++jh) {
+            const int q0 = 4 * i + 2 * jh;
+            const float2 a2 = jh == 0 ? make_float2(a4.x, a4.y) : make_float2(a4.z, a4.w);
+            const float2 c2 = jh == 0 ? make_float2(c4.x, c4.y) : make_float2(c4.z, c4.w);
+            if (q0 + 1 < C::Q) {
+              const float2 dq2 = __ffma2_rn(oms2, h2[p][q0 / 2], __fadd2_rn(a2, make_float2(-c2.x, -c2.y)));
+              dd2 = __ffma2_rn(dq2, dq2, dd2);
+            } else if (q0 < C::Q) {
+              const float dq = fmaf(oms, h1[p], a2.x - c2.x);
               dd = fmaf(dq, dq, dd);
             }
           }
         }
+        dd += dd2.x + dd2.y;
         asm volatile("" ::: "memory");
       }
     }
@@ -389,16 +418,33 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
       for (int i = 0; i < C::NQR; ++i) {
         float acc4[4] = {0.f, 0.f, 0.f, 0.f};
         if (i < C::NQA) {
+          float2 accp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          float acc1 = 0.f;
 #pragma unroll
           for (int p = 0; p < C::P; ++p) {
             const float4 a4 = load_quad<C>(sm.pts + (pg + p * C::NG) * C::DP + g * C::QA, i, last);
+            const float2 sp2 = make_float2(s[p], s[p]);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int q = 4 * i + c;
-              if (q < C::Q) {
-                acc4[c] = fmaf(s[p], h[p][q], acc4[c]);
-                h[p][q] = fmaf(s[p], h[p][q], -f4get(a4, c));
+            for (int jh = 0; jh < 2; ++jh) {
+              const int q0 = 4 * i + 2 * jh;
+              const float2 na2 = jh == 0 ? make_float2(-a4.x, -a4.y) : make_float2(-a4.z, -a4.w);
+              if (q0 + 1 < C::Q) {
+                accp[jh] = __ffma2_rn(sp2, h2[p][q0 / 2], accp[jh]);
+                h2[p][q0 / 2] = __ffma2_rn(sp2, h2[p][q0 / 2], na2);
+              } else if (q0 < C::Q) {
+                acc1 = fmaf(s[p], h1[p], acc1);
+                h1[p] = fmaf(s[p], h1[p], na2.x);
               }
+            }
+          }
+#pragma unroll
+          for (int jh = 0; jh < 2; ++jh) {
+            const int q0 = 4 * i + 2 * jh;
+            if (q0 + 1 < C::Q) {
+              acc4[2 * jh] = accp[jh].x;
+              acc4[2 * jh + 1] = accp[jh].y;
+            } else if (q0 < C::Q) {
+              acc4[2 * jh] = acc1;
             }
           }
         }
@@ -422,17 +468,30 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
         const float4 tv = h2 == 0 ? t0 : t1;
         const int sg = col / C::NQR, quad = col - sg * C::NQR;
         const int real = slice_real<C>(sg, d);
+        // this lane's four slots of z, c and sum g as one 16-byte access each (slots past the
+        // slice's real coordinates stay zero)
+        const bool has_z = quad < C::NQA;
+        const int vi0 = sg * C::QA + 4 * quad;
+        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), c4o = z4, s4o = z4;
+        if (has_z) {
+          z4 = *reinterpret_cast<const float4*>(sm.zv + vi0);
+          if (check) {
+            c4o = *reinterpret_cast<const float4*>(sm.cv + vi0);
+            s4o = *reinterpret_cast<const float4*>(sm.sgv + vi0);
+          }
+        }
+        float zn[4], cn[4], sn[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int slot = 4 * quad + i;
           const float A = f4get(tv, i);
+          zn[i] = cn[i] = sn[i] = 0.f;
           if (slot < real) {
-            const int vi = sg * C::QA + slot;
-            const float z = sm.zv[vi];
+            const float z = f4get(z4, i);
             const float znew = clampf(fmaf(-A, inv_n, z), prm.lo, prm.hi);
             if (check) {
-              const float c = sm.cv[vi];
-              const float sgp = sm.sgv[vi];
+              const float c = f4get(c4o, i);
+              const float sgp = f4get(s4o, i);
               const float del = c - znew;          // delta = c(t) - z(t+1)
               const float SD = sgp - A;            // sum_k (g_k(t) - g_k(t+1))
               const float dz = z - znew;
@@ -443,14 +502,19 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
               p_dz = fmaf(dz, dz, p_dz);
               p_dzA = fmaf(dz, A, p_dzA);
             }
-            sm.zv[vi] = znew;
-            sm.cv[vi] = 2.f * znew - z;
-            sm.sgv[vi] = A;
+            zn[i] = znew;
+            cn[i] = 2.f * znew - z;
+            sn[i] = A;
           } else if (slot == C::Q) {
             p_E += A;
           } else if (slot == C::Q + 1) {
             p_G += A;
           }
+        }
+        if (has_z) {
+          *reinterpret_cast<float4*>(sm.zv + vi0) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+          *reinterpret_cast<float4*>(sm.cv + vi0) = make_float4(cn[0], cn[1], cn[2], cn[3]);
+          *reinterpret_cast<float4*>(sm.sgv + vi0) = make_float4(sn[0], sn[1], sn[2], sn[3]);
         }
       }
       if (check) {
