@@ -79,7 +79,7 @@ KERNEL_SOURCES = ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879
                   "paper_1501_03879_gb300/csrc/shapes.h"]
 PROFILED_TRAFFIC = {
     # sources hash: {kernel: bytes per full launch}
-    "3ec88da860103f33": {"nlem_kernel": 154368 * 16, "em_batch_kernel": 366006272 * 64},
+    "4e0bea8330835c17": {"nlem_kernel": (132864 + 271104) * 16, "em_batch_kernel": (361570560 + 4096256) * 64},
 }
 
 
