@@ -414,6 +414,10 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     // h = s e - a; only four accumulators are live at once
     {
       float4* my = sm.wred + (warp * 32 + lane) * C::NQR;
+      const float* abase = sm.pts + pg * C::DP + g * C::QA;
+      // two point quads in flight ahead of their use (linear order: quad-major, point-minor)
+      float4 a_n1 = load_quad<C>(abase, 0, last);
+      float4 a_n2 = C::P > 1 ? load_quad<C>(abase + C::NG * C::DP, 0, last) : load_quad<C>(abase, 1, last);
 #pragma unroll
       for (int i = 0; i < C::NQR; ++i) {
         float acc4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -422,7 +426,13 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
           float acc1 = 0.f;
 #pragma unroll
           for (int p = 0; p < C::P; ++p) {
-            const float4 a4 = load_quad<C>(sm.pts + (pg + p * C::NG) * C::DP + g * C::QA, i, last);
+            const float4 a4 = a_n1;
+            a_n1 = a_n2;
+            {
+              const int lin = i * C::P + p + 2;          // the quad two steps ahead
+              const int ni = lin / C::P, np = lin % C::P;
+              if (ni < C::NQA) a_n2 = load_quad<C>(abase + np * C::NG * C::DP, ni, last);
+            }
             const float2 sp2 = make_float2(s[p], s[p]);
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
