@@ -24,6 +24,8 @@ constexpr int kBR = 8, kBC = 16, kBM = kBR * kBC;   // pixel block
 constexpr int kN = 256;                             // centres per MMA chunk
 constexpr uint32_t kTmemCols = 256;                 // FP32 accumulator tile 128 x 256
 constexpr uint32_t kWaitTries = 1u << 22;           // bound on mbarrier polls
+constexpr int kScrRow = 36;                          // floats per lane of epilogue scratch (16-byte rows,
+                                                     // conflict-free 16-byte stores across 8 lanes)
 
 // tcgen05 shared-memory matrix descriptor for a K-major operand without swizzling: core
 // matrices of 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo = byte
@@ -92,6 +94,32 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Pack one K x K patch (its top-left corner at src, tile row stride TC) into row n of a
+// K-major, non-swizzled operand: element (n, k) at (n / 8) * SBO + (k / 8) * 128 + (n % 8) * 16
+// + (k % 8) * 2 bytes.  Returns the FP32 squared norm of the (unrounded) patch, summed in k
+// order.  zero: stage a row of zeros (no centre).
+template <int K, int KP>
+__device__ __forceinline__ float stage_patch(const float* __restrict__ src, int TC, uint8_t* __restrict__ dst, int n,
+                                             bool zero) {
+  constexpr int D = K * K, NKC = KP / 8;
+  constexpr uint32_t SBO = NKC * 128;
+  uint8_t* row = dst + (n / 8) * SBO + (n % 8) * 16;
+  float norm = 0.f;
+#pragma unroll
+  for (int kc = 0; kc < NKC; ++kc) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc * 8 + e;
+      v[e] = (k < D && !zero) ? src[(k / K) * TC + (k % K)] : 0.f;
+      if (k < D) norm = fmaf(v[e], v[e], norm);
+    }
+    *reinterpret_cast<uint4*>(row + kc * 128) =
+        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  }
+  return norm;
+}
+
 template <int K, int KP>
 __global__ void __launch_bounds__(kBM, 1)
 bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2,
@@ -112,6 +140,8 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
   const int UR = kBR + 2 * R, UC = kBC + 2 * R, NU = UR * UC;   // union window centres
   const int TR = UR + 2 * HK, TC = UC + 2 * HK;
   float* unorm = tile + TR * TC;                                // ||P_u||^2 per centre
+  float* scratch = reinterpret_cast<float*>(
+      reinterpret_cast<uintptr_t>(unorm + NU + 3) & ~(uintptr_t)15);  // [128][kScrRow], 16-byte aligned
 
   if (warp == 0) {
     tmem_alloc(&s_tmem, kTmemCols);
@@ -123,48 +153,25 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
   }
   // tile of the reflect-padded image: union centre (ur, uc) is image (r0-R+ur, c0-R+uc) and
   // its patch is tile[ur .. ur+K-1][uc .. uc+K-1]
-  for (int i = t; i < TR * TC; i += kBM) {
-    const int tr = i / TC, tc = i - tr * TC;
-    tile[i] = __ldg(img + (size_t)reflect_clamped(r0 - R - HK + tr, H) * pitch + reflect_clamped(c0 - R - HK + tc, W));
+  for (int tr = warp; tr < TR; tr += kBM / 32) {   // a warp per tile row, lanes along it
+    const float* grow = img + (size_t)reflect_clamped(r0 - R - HK + tr, H) * pitch;
+    for (int tc = t & 31; tc < TC; tc += 32) tile[tr * TC + tc] = __ldg(grow + reflect_clamped(c0 - R - HK + tc, W));
   }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tmem_d = s_tmem;
 
-  // A: the block's patches; pixel m = (m / 16, m % 16) sits at union centre (mr+R, mc+R)
-  for (int idx = t; idx < kBM * NKC; idx += kBM) {
-    const int m = idx % kBM, kc = idx / kBM;
-    const int mr = m / kBC, mc = m % kBC;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int k = kc * 8 + e;
-      v[e] = k < D ? tile[(mr + R + k / K) * TC + (mc + R + k % K)] : 0.f;
-    }
-    uint4 q = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-    *reinterpret_cast<uint4*>(Asm + (m / 8) * SBO + kc * 128 + (m % 8) * 16) = q;
-  }
-  for (int u = t; u < NU; u += kBM) {
-    const int ur = u / UC, uc = u - ur * UC;
-    float s = 0.f;
-    for (int k = 0; k < D; ++k) {
-      const float x = tile[(ur + k / K) * TC + (uc + k % K)];
-      s = fmaf(x, x, s);
-    }
-    unorm[u] = s;
-  }
-  // this thread's pixel
+  // A: the block's patches, a thread per pixel; pixel m = (m / 16, m % 16) sits at union
+  // centre (mr+R, mc+R).  Its FP32 norm comes out of the same pass.
   const int mr = t / kBC, mc = t % kBC;
+  const float pnorm = stage_patch<K, KP>(tile + (mr + R) * TC + (mc + R), TC, Asm, t, false);
   const int pr = r0 + mr, pc = c0 + mc;
   const bool pix_ok = pr < H && pc < W;
-  float pnorm = 0.f;
-  for (int k = 0; k < D; ++k) {
-    const float x = tile[(mr + R + k / K) * TC + (mc + R + k % K)];
-    pnorm = fmaf(x, x, pnorm);
-  }
-  const int rw0 = max(pr - R, 0), cw0 = max(pc - R, 0);
-  const int nwc = min(pc + R, W - 1) - cw0 + 1;
+  // this pixel's search window clipped to the image, in union coordinates
+  const int ur_lo = max(pr - R, 0) - r0 + R, ur_hi = min(pr + R, H - 1) - r0 + R;
+  const int uc_lo = max(pc - R, 0) - c0 + R, uc_hi = min(pc + R, W - 1) - c0 + R;
+  const int nwc = uc_hi - uc_lo + 1;
   float* wrow = wtab + ((size_t)pr * W + pc) * (size_t)(S * S);
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, kN);
   bool ok = true;
@@ -172,23 +179,13 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
 
   const int nchunks = (NU + kN - 1) / kN;
   for (int ch = 0; ch < nchunks; ++ch) {
-    for (int idx = t; idx < kN * NKC; idx += kBM) {   // B: this chunk's centres
-      const int nn = idx % kN, kc = idx / kN;
+    // B: this chunk's centres, a thread per centre (and its FP32 norm)
+    for (int nn = t; nn < kN; nn += kBM) {
       const int u = ch * kN + nn;
-      float v[8];
-      if (u < NU) {
-        const int ur = u / UC, uc = u - ur * UC;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int k = kc * 8 + e;
-          v[e] = k < D ? tile[(ur + k / K) * TC + (uc + k % K)] : 0.f;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0.f;
-      }
-      uint4 q = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-      *reinterpret_cast<uint4*>(Bsm + (nn / 8) * SBO + kc * 128 + (nn % 8) * 16) = q;
+      const bool live = u < NU;
+      const int ur = live ? u / UC : 0, uc = live ? u - ur * UC : 0;
+      const float nrm = stage_patch<K, KP>(tile + ur * TC + uc, TC, Bsm, nn, !live);
+      if (live) unorm[u] = nrm;
     }
     fence_proxy_async_smem();
     tmem_fence_before_sync();
@@ -209,24 +206,31 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
       break;
     }
     tmem_fence_after_sync();
-    // row t of D: this pixel against the chunk's 256 centres
+    // row t of D: this pixel against the chunk's 256 centres, 32 columns at a time.  The 32
+    // dot products go to this lane's own scratch row (16-byte stores), and the lane then walks
+    // only its own window's columns in the block: a run per union row, at most three rows.
     const uint32_t trow = tmem_d + ((uint32_t)(warp * 32) << 16);
+    float* my = scratch + t * kScrRow;
 #pragma unroll 1
     for (int cb = 0; cb < kN; cb += 32) {
+      const int u0 = ch * kN + cb;
+      if (u0 >= NU) break;                       // the same for every thread
       uint32_t v[32];
       tmem_ld32(trow + cb, v);
       tmem_wait_ld(v);
       if (!pix_ok) continue;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const int u = ch * kN + cb + e;
-        if (u >= NU) break;
-        const int ur = u / UC, uc = u - ur * UC;
-        const int dr = ur - mr - R, dc = uc - mc - R;
-        const int ir = r0 - R + ur, ic = c0 - R + uc;
-        if (dr < -R || dr > R || dc < -R || dc > R || ir < 0 || ir >= H || ic < 0 || ic >= W) continue;
-        const float D2 = fmaxf(pnorm + unorm[u] - 2.f * __uint_as_float(v[e]), 0.f);
-        wrow[(ir - rw0) * nwc + (ic - cw0)] = expf(-D2 * inv_h2);
+      for (int e = 0; e < 32; e += 4)
+        *reinterpret_cast<float4*>(my + e) = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                                         __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+      const int uend = min(u0 + 32, NU);          // exclusive
+      for (int ur = max(u0 / UC, ur_lo); ur <= ur_hi && ur * UC < uend; ++ur) {
+        const int a = max(ur * UC + uc_lo, u0), b = min(ur * UC + uc_hi + 1, uend);
+        float* dst = wrow + (ur - ur_lo) * nwc - (ur * UC + uc_lo);   // indexed by u
+        for (int u = a; u < b; ++u) {
+          const float D2 = fmaxf(pnorm + unorm[u] - 2.f * my[u - u0], 0.f);
+          dst[u] = expf(-D2 * inv_h2);
+        }
       }
     }
     tmem_fence_before_sync();
@@ -244,7 +248,8 @@ int launch_weights(const float* img, int H, int W, int pitch, int S, float inv_h
                    cudaStream_t stream) {
   const int R = (S - 1) / 2;
   const int TR = kBR + 2 * R + (K - 1), TC = kBC + 2 * R + (K - 1);
-  const size_t smem = (size_t)kBM * KP * 2 + (size_t)kN * KP * 2 + ((size_t)TR * TC + (size_t)(kBR + 2 * R) * (kBC + 2 * R)) * 4;
+  const size_t smem = (size_t)kBM * KP * 2 + (size_t)kN * KP * 2 +
+                      ((size_t)TR * TC + (size_t)(kBR + 2 * R) * (kBC + 2 * R) + 4 + (size_t)kBM * kScrRow) * 4;
   if (smem > 200 * 1024) return -1;
   auto kern = bf16_weights_kernel<K, KP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -258,6 +263,7 @@ int launch_weights(const float* img, int H, int W, int pitch, int S, float inv_h
 
 int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, int S, float inv_h2, float* wtab,
                         int* err, cudaStream_t stream) {
+  if (S < 1 || S > 31) return -1;   // the compiled range (window <= 31)
   switch (patch) {
     case 5: return launch_weights<5, 32>(img, H, W, pitch, S, inv_h2, wtab, err, stream);
     case 7: return launch_weights<7, 64>(img, H, W, pitch, S, inv_h2, wtab, err, stream);
