@@ -170,3 +170,40 @@ def test_trained_warm_start_gains_over_plain_admm(nl):
         zo, *_ = oracle.em_admm(pts, w, 0.0, 255.0, float(rho[lin]), int(used[lin]), z0=np.clip(x0[lin], 0, 255))
         assert rel_err(out[lin], zo[24]) <= TOL
     ws.close()
+
+
+def test_warm_start_full_size_sampled(nl):
+    """The learned-start path at the benchmark's size (2048x2048, sigma 25, 7x7 patches, 21x21
+    window, tol 1e-4 every 10, cap 300): each sampled pixel equals the oracle replayed for the
+    iterations the GPU ran, from the network's start and penalty, or, where the warm-started
+    solve reached the cap, from the weighted mean at rho = 1 (the fallback)."""
+    from paper_1501_03879_gb300 import warmstart as wst
+    train = [torch.from_numpy(synth.noisy_image(8400, 96, 96, 25.0)[0]).to(DEV)]
+    feats, tgt, _ = wst.make_training_set(train, [250.0], per_image=4096, seed=2)
+    ws = nl.WarmStart(49, seed=11)
+    wst.train(ws, feats, tgt, epochs=10, batch=512, lr=2e-3, seed=2)
+    Hs = Ws = 2048
+    g, _ = synth.noisy_image(8500, Hs, Ws, 25.0)
+    img = torch.from_numpy(g).to(DEV)
+    kw = dict(iters=300, tol=1e-4, check_every=10)
+    r = nl.nlem_denoise_warm(ws, img, 7, 21, 250.0, rho_fallback=1.0, **kw)
+    out = r["out"].cpu().numpy().reshape(-1)
+    used = r["iters_used"].cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(12)
+    pix = np.unique(np.concatenate([[0, Ws - 1, Ws * (Hs - 1), Hs * Ws - 1, 1000 * Ws + 5, 7 * Ws + 2040],
+                                    rng.integers(0, Hs * Ws, 6)])).astype(np.int32)
+    _, x0, rho = ws.predict(nl.nlem_features(img, 7, 21, 250.0))
+    x0, rho = x0.cpu().numpy(), rho.cpu().numpy()
+    # the warm-started solve alone, on the sampled pixels: which of them fell back
+    ex = nl.nlem_denoise_ex(img, 7, 21, 250.0, rho=1.0, pixels=torch.from_numpy(pix).to(DEV),
+                            x0=torch.from_numpy(x0).to(DEV), rho_pix=torch.from_numpy(rho).to(DEV), **kw)
+    used_ex = ex["iters_used"].cpu().numpy().reshape(-1)[pix]
+    for lin, uex in zip(pix, used_ex):
+        pts, w, _ = oracle.nlem_problem(g, 7, 21, 250.0, int(lin))
+        if uex < 300:
+            assert used[lin] == uex
+            zo, *_ = oracle.em_admm(pts, w, 0.0, 255.0, float(rho[lin]), int(uex), z0=np.clip(x0[lin], 0, 255))
+        else:
+            zo, *_ = oracle.em_admm(pts, w, 0.0, 255.0, 1.0, int(used[lin]))
+        assert rel_err(out[lin], zo[24]) <= TOL, (int(lin), int(uex), int(used[lin]))
+    ws.close()
