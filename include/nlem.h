@@ -248,6 +248,15 @@ int nlem_ws_loss_grad(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, con
 /* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the loss of the batch. */
 int nlem_ws_train_step(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long B,
                        float lr, float* loss, void* stream);
+/* Training on a whole set: `epochs` passes over feats [N][2d+2] and targets [N][d+1] (device),
+ * each in a fresh order (a Fisher-Yates shuffle drawn from SplitMix64 in counter mode under
+ * `seed`), one nlem_ws_train_step per full minibatch of `batch` rows (min(batch, N); the
+ * N mod batch rows an epoch leaves out come up in later epochs' orders).  epoch_loss: host
+ * [epochs] or NULL, the mean minibatch loss of each epoch (reading it waits for the device).
+ * The library owns the order and minibatch workspace inside ws.  Errors: -1 for N < 1,
+ * epochs < 0, batch < 1 or lr not finite and > 0; -5 for N >= 2^31. */
+int nlem_ws_train(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long N,
+                  int epochs, int batch, float lr, unsigned long long seed, float* epoch_loss, void* stream);
 /* y = network(feats), then x0 [B][d] and rho [B] as above (device arrays). */
 int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, nlem_box box, float* y,
                     float* x0, float* rho, void* stream);

@@ -84,6 +84,7 @@ def load_library():
         lib.nlem_ws_forward.argtypes = [vp, vp, vp, ll, vp, vp]
         lib.nlem_ws_loss_grad.argtypes = [vp, vp, vp, vp, ll, vp, vp, vp]
         lib.nlem_ws_train_step.argtypes = [vp, vp, vp, vp, ll, f, vp, vp]
+        lib.nlem_ws_train.argtypes = [vp, vp, vp, vp, ll, i, i, f, ctypes.c_ulonglong, vp, vp]
         lib.nlem_ws_predict.argtypes = [vp, vp, vp, ll, _Box, vp, vp, vp, vp]
         lib.nlem_features.argtypes = [vp, vp, i, i, i, i, i, f, vp, ll, vp, vp]
         lib.nlem_denoise_ex.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, ll, vp, vp,
@@ -454,6 +455,17 @@ class WarmStart:
         B = feats.shape[0]
         _check(load_library().nlem_ws_train_step(self.ctx.handle, self.handle, _ptr(feats), _ptr(targets), B,
                                                  float(lr), _ptr(loss), _stream(feats.device)))
+
+    def train(self, feats, targets, epochs, batch, lr, seed=0):
+        """`epochs` shuffled passes of minibatch Adam over the whole set (nlem_ws_train);
+        returns the mean minibatch loss of each epoch."""
+        import numpy as np
+        N = feats.shape[0]
+        hist = np.zeros(max(int(epochs), 1), dtype=np.float32)
+        _check(load_library().nlem_ws_train(self.ctx.handle, self.handle, _ptr(feats), _ptr(targets), N, int(epochs),
+                                            int(batch), float(lr), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                            hist.ctypes.data_as(ctypes.c_void_p), _stream(feats.device)))
+        return [float(x) for x in hist[:int(epochs)]]
 
     def predict(self, feats, box=(0.0, 255.0)):
         import torch

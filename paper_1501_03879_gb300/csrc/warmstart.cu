@@ -257,6 +257,15 @@ __global__ void fallback_list_kernel(const int* __restrict__ iters_used, long lo
   }
 }
 
+__global__ void gather_rows_kernel(const float* __restrict__ src, int cols, const int* __restrict__ rows,
+                                   long long nrows, float* __restrict__ dst) {
+  const long long total = nrows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols;
+    dst[i] = src[(long long)rows[r] * cols + (i - r * cols)];
+  }
+}
+
 int grid_for(long long n, int threads, int sm_count) {
   long long g = (n + threads - 1) / threads;
   const long long cap = (long long)sm_count * 16;
@@ -320,6 +329,12 @@ int ws_apply(const float* feats, const float* y, long long B, int d, float lo, f
              int sm_count, cudaStream_t s) {
   if (B <= 0) return 0;
   apply_kernel<<<grid_for(B * d, 256, sm_count), 256, 0, s>>>(feats, y, B, d, lo, hi, x0, rho);
+  return (int)cudaGetLastError();
+}
+
+int ws_gather_rows(const float* src, int cols, const int* rows, long long nrows, float* dst, int sm_count,
+                   cudaStream_t s) {
+  gather_rows_kernel<<<grid_for(nrows * cols, 256, sm_count), 256, 0, s>>>(src, cols, rows, nrows, dst);
   return (int)cudaGetLastError();
 }
 

@@ -36,6 +36,9 @@ int ws_adam(WsModel& m, const float* grad, float lr, int sm_count, cudaStream_t 
 int ws_sync_half(WsModel& m, int sm_count, cudaStream_t s);
 int ws_apply(const float* feats, const float* y, long long B, int d, float lo, float hi, float* x0, float* rho,
              int sm_count, cudaStream_t s);
+// dst[r][c] = src[rows[r]][c] for r < nrows, c < cols (minibatch gather).
+int ws_gather_rows(const float* src, int cols, const int* rows, long long nrows, float* dst, int sm_count,
+                   cudaStream_t s);
 int ws_fallback_list(const int* iters_used, long long npix, int cap, int* list, long long* count, int sm_count,
                      cudaStream_t s);
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/nlem.h"
@@ -19,6 +20,12 @@ struct nlem_warmstart {
   nlem_ctx* ctx = nullptr;
   nlemk::WsModel m;
   nlemk::WsScratch sc;
+  // minibatch workspace of nlem_ws_train: sample order, gathered rows, per-step losses
+  int* perm = nullptr;
+  float* fb = nullptr;
+  float* tb = nullptr;
+  float* losses = nullptr;
+  size_t cap_perm = 0, cap_fb = 0, cap_tb = 0, cap_losses = 0;
 };
 
 namespace {
@@ -181,6 +188,10 @@ int nlem_ws_destroy(nlem_warmstart* ws) {
   cudaFree(ws->sc.da1);
   cudaFree(ws->sc.da2);
   cudaFree(ws->sc.grad);
+  cudaFree(ws->perm);
+  cudaFree(ws->fb);
+  cudaFree(ws->tb);
+  cudaFree(ws->losses);
   delete ws;
   return NLEM_OK;
 }
@@ -302,6 +313,64 @@ int nlem_ws_train_step(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, co
   if (rc) return rc;
   rc = nlemk::ws_adam(ws->m, ws->sc.grad, lr, ctx->sm_count, (cudaStream_t)stream);
   return rc ? wcuda((cudaError_t)rc, "Adam step") : NLEM_OK;
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014), used in counter mode for the epoch
+// orders of nlem_ws_train.
+static unsigned long long ws_mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int nlem_ws_train(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long N,
+                  int epochs, int batch, float lr, unsigned long long seed, float* epoch_loss, void* stream) {
+  if (!ctx || !ws || !feats || !targets || N < 1 || epochs < 0 || batch < 1 || !(lr > 0.f) || !std::isfinite(lr))
+    return wfail(NLEM_ERR_INVALID, "bad arguments");
+  if (N > 2147483647LL) return wfail(NLEM_ERR_UNSUPPORTED, "at most 2^31 - 1 samples");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = ws->m.d, F = 2 * d + 2, O = d + 1;
+  const long long B = batch < N ? batch : N;
+  const long long steps = N / B;   // full minibatches; the remainder joins a later epoch's order
+  int rc;
+  if (N > (long long)ws->cap_perm || B * F > (long long)ws->cap_fb || B * O > (long long)ws->cap_tb ||
+      steps > (long long)ws->cap_losses)
+    cudaStreamSynchronize(s);
+  if ((rc = grow(&ws->perm, &ws->cap_perm, (size_t)N, "sample order"))) return rc;
+  if ((rc = grow(&ws->fb, &ws->cap_fb, (size_t)(B * F), "minibatch features"))) return rc;
+  if ((rc = grow(&ws->tb, &ws->cap_tb, (size_t)(B * O), "minibatch targets"))) return rc;
+  if ((rc = grow(&ws->losses, &ws->cap_losses, (size_t)steps, "losses"))) return rc;
+  std::vector<int> order((size_t)N);
+  std::vector<float> lh((size_t)steps);
+  for (int ep = 0; ep < epochs; ++ep) {
+    // Fisher-Yates shuffle; draw i of epoch ep is mix64(key_ep + (i + 1) * golden)
+    for (long long i = 0; i < N; ++i) order[(size_t)i] = (int)i;
+    const unsigned long long key = ws_mix64(seed ^ (0x9E3779B97F4A7C15ull * (unsigned long long)(ep + 1)));
+    for (long long i = N - 1; i > 0; --i) {
+      const unsigned long long r = ws_mix64(key + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull);
+      const long long j = (long long)(r % (unsigned long long)(i + 1));
+      std::swap(order[(size_t)i], order[(size_t)j]);
+    }
+    cudaError_t e = cudaMemcpyAsync(ws->perm, order.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host order is rewritten next epoch
+    if (e != cudaSuccess) return wcuda(e, "sample order upload");
+    for (long long k = 0; k < steps; ++k) {
+      int ge = nlemk::ws_gather_rows(feats, F, ws->perm + k * B, B, ws->fb, ctx->sm_count, s);
+      if (!ge) ge = nlemk::ws_gather_rows(targets, O, ws->perm + k * B, B, ws->tb, ctx->sm_count, s);
+      if (ge) return wcuda((cudaError_t)ge, "minibatch gather");
+      if ((rc = nlem_ws_train_step(ctx, ws, ws->fb, ws->tb, B, lr, ws->losses + k, stream))) return rc;
+    }
+    if (epoch_loss) {
+      e = cudaMemcpyAsync(lh.data(), ws->losses, (size_t)steps * sizeof(float), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return wcuda(e, "read losses");
+      double acc = 0.0;
+      for (long long k = 0; k < steps; ++k) acc += lh[(size_t)k];
+      epoch_loss[ep] = (float)(acc / (double)steps);
+    }
+  }
+  return NLEM_OK;
 }
 
 int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, nlem_box box, float* y,

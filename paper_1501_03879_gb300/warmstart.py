@@ -5,7 +5,7 @@ For each training image, a seeded sample of pixels is solved (nlem_denoise_ex, t
 that reaches the tolerance in the fewest iterations, and the label start point is the solution
 patch of a tight solve (tolerance 1e-6) with that penalty.  Targets for the network output y:
 y[0:d] = (z* - m) / 16 and y[d] = ln rho*.  Training runs the library's forward, backward and
-Adam kernels on minibatches; torch is used only to hold device arrays and to shuffle indices.
+Adam kernels on shuffled minibatches (nlem_ws_train); torch only holds device arrays.
 """
 from __future__ import annotations
 
@@ -61,30 +61,10 @@ def make_training_set(images, hs, patch=7, window=21, per_image=4096, seed=0, to
     return torch.cat(feats_all), torch.cat(tgt_all), info
 
 
-def train(ws: B.WarmStart, feats, targets, epochs=10, batch=4096, lr=1e-3, seed=0, log_every=0):
-    """Adam on minibatches of the training set; returns the mean loss of each epoch."""
-    import torch
-    N = feats.shape[0]
-    g = torch.Generator(device=feats.device)
-    g.manual_seed(seed)
-    loss = torch.zeros(1, dtype=torch.float32, device=feats.device)
-    history = []
-    for ep in range(epochs):
-        perm = torch.randperm(N, generator=g, device=feats.device)
-        tot, nb = 0.0, 0
-        for s in range(0, N - batch + 1 if N >= batch else 1, batch):
-            idx = perm[s:s + batch]
-            f = feats[idx].contiguous()
-            t = targets[idx].contiguous()
-            ws.train_step(f, t, lr, loss=loss)
-            tot += float(loss.item()) if log_every else 0.0
-            nb += 1
-        if log_every:
-            history.append(tot / max(nb, 1))
-        else:
-            l, _ = ws.loss_grad(feats[:min(N, 16384)].contiguous(), targets[:min(N, 16384)].contiguous())
-            history.append(float(l.item()))
-    return history
+def train(ws: B.WarmStart, feats, targets, epochs=10, batch=4096, lr=1e-3, seed=0):
+    """Adam on shuffled minibatches of the training set, entirely in the library
+    (nlem_ws_train); returns the mean minibatch loss of each epoch."""
+    return ws.train(feats.contiguous(), targets.contiguous(), epochs, batch, lr, seed)
 
 
 def evaluate(ws: B.WarmStart, image, h, patch=7, window=21, cap=300, tol=1e-4, check_every=10, rho_plain=1.0,

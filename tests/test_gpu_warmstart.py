@@ -207,3 +207,36 @@ def test_warm_start_full_size_sampled(nl):
             zo, *_ = oracle.em_admm(pts, w, 0.0, 255.0, 1.0, int(used[lin]))
         assert rel_err(out[lin], zo[24]) <= TOL, (int(lin), int(uex), int(used[lin]))
     ws.close()
+
+
+def test_ws_train_matches_steps_and_is_seeded(nl):
+    """nlem_ws_train: one epoch with the whole set as the minibatch equals one Adam step on the
+    set (the order only changes the summation order), its reported loss is the set's loss, the
+    same seed reproduces the same parameters and another seed orders the minibatches
+    differently."""
+    d = 25
+    rng = np.random.default_rng(21)
+    N = 96
+    feats = torch.from_numpy(np.concatenate([rng.uniform(0, 255, (N, 2 * d)), rng.uniform(3, 6, (N, 1)),
+                                             rng.uniform(0, 0.3, (N, 1))], axis=1).astype(np.float32)).to(DEV)
+    tgt = torch.from_numpy(rng.normal(size=(N, d + 1)).astype(np.float32)).to(DEV)
+    lr = 1e-3
+    a, b = nl.WarmStart(d, seed=4), nl.WarmStart(d, seed=4)
+    loss0, _ = a.loss_grad(feats, tgt)
+    a.train_step(feats, tgt, lr)
+    hist = b.train(feats, tgt, epochs=1, batch=N, lr=lr, seed=9)
+    assert abs(hist[0] - loss0.item()) <= 1e-5 * loss0.item()
+    pa, pb = a.get_params(), b.get_params()
+    close = np.abs(pa - pb) <= 1e-6 * np.maximum(1.0, np.abs(pa)) + 1e-3 * lr
+    assert close.mean() >= 0.999      # a first Adam step is lr*sign(g): gradients at rounding level may flip
+    c1, c2, c3 = nl.WarmStart(d, seed=5), nl.WarmStart(d, seed=5), nl.WarmStart(d, seed=5)
+    h1 = c1.train(feats, tgt, epochs=3, batch=16, lr=lr, seed=1)
+    c2.train(feats, tgt, epochs=3, batch=16, lr=lr, seed=1)
+    c3.train(feats, tgt, epochs=3, batch=16, lr=lr, seed=2)
+    assert np.array_equal(c1.get_params(), c2.get_params())
+    assert not np.array_equal(c1.get_params(), c3.get_params())
+    assert len(h1) == 3 and all(np.isfinite(h1))
+    with pytest.raises(nl.NlemError):
+        c1.train(feats, tgt, epochs=1, batch=0, lr=lr)
+    for m in (a, b, c1, c2, c3):
+        m.close()
