@@ -97,8 +97,9 @@ int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, in
  *            (scaled-form ADMM residuals of Boyd et al. 2011, as cited in Sec. 2)
  *   obj64 / kkt64 [B] double or NULL (only with opt->fp64_check): F(z) of problem (1) and
  *            the projected-gradient optimality residual ||z - P_C(z - g/sum w)||, both in FP64.
- * Errors as em_solve; -5 if n exceeds the largest problem the on-chip kernels hold for this
- * d and no workspace could be created for the streaming kernel.
+ * Errors as em_solve; -5 if n exceeds the largest problem the on-chip (register + shared
+ * memory) kernels hold for this d: 896 points for d = 25 and 49, 448 for d = 81, and for other
+ * d <= 28 / 60 / 120: 512 / 256 / 256.
  */
 int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n,
                    int d, nlem_box box, float rho, int iters, const float* x0,
