@@ -54,8 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--profile-case", choices=["traffic"], default=None,
-                   help="run the small profiling case (no timing output) and exit")
+    p.add_argument("--profile-case", choices=["traffic", "bf16", "features"], default=None,
+                   help="run a small profiling case (no timing output) and exit")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra rows (rho=1e-3, mixed precision, batch, learned warm start)")
     p.add_argument("--ws-train", type=int, default=131072, help="training solves for the learned warm start")
@@ -79,7 +79,7 @@ KERNEL_SOURCES = ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879
                   "paper_1501_03879_gb300/csrc/shapes.h"]
 PROFILED_TRAFFIC = {
     # sources hash: {kernel: bytes per full launch}
-    "4e0bea8330835c17": {"nlem_kernel": (132864 + 271104) * 16, "em_batch_kernel": (361570560 + 4096256) * 64},
+    "4c4a3301755d6e1f": {"nlem_kernel": (194816 + 206336) * 16, "em_batch_kernel": (362041344 + 4086784) * 64},
 }
 
 
@@ -92,13 +92,26 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def profile_case():
-    """The small case of the counter capture: NLEM on a 128x128 image and 4096 standalone
-    problems, with the benchmark's per-problem settings; each call twice."""
+def profile_case(which="traffic"):
+    """Small cases for counter captures, each call made twice.
+    traffic: NLEM on a 128x128 image and 4096 standalone problems with the benchmark's
+    per-problem settings.  bf16: the tensor-core weight table of a 256x256 image (sigma 30 + 5%
+    impulses, 9x9 patches, 21x21 window).  features: the warm-start features of a 256x256 image
+    (7x7 patches, 21x21 window)."""
     import torch
     import synth
     import paper_1501_03879_gb300 as nl
     dev = torch.device("cuda", 0)
+    if which in ("bf16", "features"):
+        g, _ = synth.noisy_image(5005, 256, 256, 30.0, salt_pepper=0.05)
+        gi = torch.from_numpy(g).to(dev)
+        for _ in range(2):
+            if which == "bf16":
+                nl.nlem_bf16_weights(gi, 9, 21, 300.0)
+            else:
+                nl.nlem_features(gi, 7, 21, 250.0)
+        torch.cuda.synchronize()
+        return
     g, _ = synth.noisy_image(10011, 128, 128, 20.0)
     gi = torch.from_numpy(g).to(dev)
     for _ in range(2):
@@ -372,6 +385,27 @@ def extra_warm_start(nl, ctx, n_train):
             "speedup_vs_plain_rho1": ms_p / ms_w, "speedup_vs_best_rho": ms_b / ms_w}
 
 
+def extra_paper_setting(nl, ctx):
+    """The paper's own denoising setting (Sec. 3): 7x7 patches, 21x21 window, h = 10 sigma,
+    mu = 1e-3, 4 iterations from the noisy patch, on the production-size synthetic images:
+    throughput, and PSNR of the noisy input, of NLM (the weighted-mean start) and of NLEM."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    for i, sg in enumerate(SIGMAS):
+        g, f = synth.noisy_image(SEED * 10 + 700 + i, H, W, sg)
+        img = torch.from_numpy(g).to(dev)
+        ms, r = _timed(lambda: nl.nlem_denoise(img, patch=K_PATCH, window=S_WIN, h=10 * sg, rho=1e-3, iters=4, box=BOX,
+                                               init=nl.INIT_NOISY_PATCH, ctx=ctx), reps=3)
+        nlm = nl.nlem_denoise(img, patch=K_PATCH, window=S_WIN, h=10 * sg, rho=1.0, iters=0, box=BOX, ctx=ctx)
+        rows.append({"sigma": sg, "mpixel_per_s": H * W / (ms * 1e-3) / 1e6,
+                     "psnr_noisy": synth.psnr(g, f), "psnr_nlm": synth.psnr(nlm["out"].cpu().numpy(), f),
+                     "psnr_nlem": synth.psnr(r["out"].cpu().numpy(), f)})
+    return {"workload": "512x512 synthetic, 7x7 patches, 21x21 window, h=10 sigma, mu=1e-3, 4 iterations, "
+                        "noisy-patch start", "rows": rows}
+
+
 def run_extras(nl, ctx, imgs, args):
     peaks = {}
     try:
@@ -382,6 +416,7 @@ def run_extras(nl, ctx, imgs, args):
         pass
     out = {}
     out["rho_1e-3"] = extra_small_rho(nl, ctx, imgs)
+    out["paper_setting"] = extra_paper_setting(nl, ctx)
     out["bf16"] = extra_mixed_precision(nl, ctx, peaks)
     out["batch"] = extra_batch(nl, ctx)
     out["warm_start"] = extra_warm_start(nl, ctx, args.ws_train)
@@ -394,7 +429,7 @@ def run_extras(nl, ctx, imgs, args):
 def main():
     args = parse()
     if args.profile_case:
-        profile_case()
+        profile_case(args.profile_case)
         return
     if args.impl == "reference":
         run_reference(args)
