@@ -1,5 +1,5 @@
 // Tensor Memory (TMEM) helpers for sm_103a: inline PTX for tcgen05 allocation, 32-column
-// loads/stores of a thread's own TMEM lane, and the waits and fences that order them.
+// loads of a thread's own TMEM lane, and the waits and fences that order them.
 //
 // TMEM is 128 lanes x 512 columns of 32-bit cells per SM; warp w of a CTA reaches lanes
 // 32*(w%4) .. 32*(w%4)+31 only.  The BF16 cross-term kernel keeps its FP32 accumulator tile
@@ -39,8 +39,6 @@ __device__ __forceinline__ void tmem_fence_after_sync() {
                    "=r"(v[i + 6]), "=r"(v[i + 7])
 #define NLEM_W8(i) "+r"(v[i]), "+r"(v[i + 1]), "+r"(v[i + 2]), "+r"(v[i + 3]), "+r"(v[i + 4]), "+r"(v[i + 5]), \
                    "+r"(v[i + 6]), "+r"(v[i + 7])
-#define NLEM_S8(i) "r"(v[i]), "r"(v[i + 1]), "r"(v[i + 2]), "r"(v[i + 3]), "r"(v[i + 4]), "r"(v[i + 5]), \
-                   "r"(v[i + 6]), "r"(v[i + 7])
 
 // Start loading 32 consecutive columns of this thread's lane into v (asynchronous: the
 // values may be read only after tmem_wait_ld(v)).  taddr must be warp-uniform.
@@ -57,24 +55,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : NLEM_W8(0), NLEM_W8(8), NLEM_W8(16), NLEM_W8(24)::"memory");
 }
-// Store 32 registers into 32 consecutive columns of this thread's lane.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      NLEM_S8(0), NLEM_S8(8), NLEM_S8(16), NLEM_S8(24)
-      : "memory");
-}
-// Wait until every TMEM store this thread issued has completed.
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
 #undef NLEM_R8
 #undef NLEM_W8
-#undef NLEM_S8
-
-__host__ __device__ constexpr uint32_t tmem_cols_pow2(int cols) {
-  return cols <= 32 ? 32u : (cols <= 64 ? 64u : (cols <= 128 ? 128u : (cols <= 256 ? 256u : 512u)));
-}
 
 }  // namespace nlemk
