@@ -71,15 +71,21 @@ def rank_workload(rank: int, world: int):
     return {"image_seeds": [SEED * 10 + i + 100 * rank for i in range(len(SIGMAS))], "em_seed": SEED + rank}
 
 
-# DRAM traffic per full launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# capture summarised in profiles/nlem_kernel_d49_counters.md, scaled from its small case by
-# units processed.  Valid only for the kernel sources it was taken on (hash below); any later
-# change of those sources reports null until a new capture is recorded here.
+# Counters of the ncu capture summarised in profiles/nlem_kernel_d49_counters.md, valid only for
+# the kernel sources they were taken on (hash below); any later change of those sources reports
+# null until a new capture is recorded here.  traffic = dram__bytes_read.sum +
+# dram__bytes_write.sum per full launch, scaled from the small case by units processed; the
+# percentages are sm__pipe_fma_cycles_active, smsp__issue_active and the shared-memory
+# wavefronts, each as a fraction of peak over the captured launch.
 KERNEL_SOURCES = ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879_gb300/csrc/solve_kernels.cuh",
                   "paper_1501_03879_gb300/csrc/shapes.h"]
-PROFILED_TRAFFIC = {
-    # sources hash: {kernel: bytes per full launch}
-    "4c4a3301755d6e1f": {"nlem_kernel": (194816 + 206336) * 16, "em_batch_kernel": (362041344 + 4086784) * 64},
+PROFILED = {
+    "4c4a3301755d6e1f": {
+        "nlem_kernel": {"traffic": (194816 + 206336) * 16, "fma_pipe_pct": 43.58, "issue_pct": 37.33,
+                        "smem_wavefront_pct": 67.66},
+        "em_batch_kernel": {"traffic": (362041344 + 4086784) * 64, "fma_pipe_pct": 41.35, "issue_pct": 36.46,
+                            "smem_wavefront_pct": 63.73},
+    },
 }
 
 
@@ -535,15 +541,22 @@ def main():
     em_ach = em_fl / (em_avg_ms / 1e3) / 1e12
     dominant = "nlem_kernel" if sum(nlem_ms) >= sum(em_ms) else "em_batch_kernel"
     ach = nlem_ach if dominant == "nlem_kernel" else em_ach
-    traffic = PROFILED_TRAFFIC.get(kernel_sources_hash(), {}).get(dominant)
+    prof = PROFILED.get(kernel_sources_hash(), {})
+    traffic = prof.get(dominant, {}).get("traffic")
+
+    def dram_gbs(kernel, avg_ms):   # profiled DRAM bytes per launch / the live launch time
+        b = prof.get(kernel, {}).get("traffic")
+        return None if b is None else b / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "kernel": dominant, "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s",
                 "frac": ach / peak_alu, "traffic": traffic,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz_max:.0f} MHz",
+                "ncu": {k: {m: v for m, v in d.items() if m != "traffic"} for k, d in prof.items()} or None,
                 "fma_chain_measured_tflops": tf_chain,
                 "per_kernel": {"nlem_kernel": {"tflops": nlem_ach, "frac": nlem_ach / peak_alu,
-                                               "avg_ms": nlem_avg_ms},
+                                               "avg_ms": nlem_avg_ms, "dram_gbs": dram_gbs("nlem_kernel", nlem_avg_ms)},
                                "em_batch_kernel": {"tflops": em_ach, "frac": em_ach / peak_alu,
-                                                   "avg_ms": em_avg_ms}}}
+                                                   "avg_ms": em_avg_ms,
+                                                   "dram_gbs": dram_gbs("em_batch_kernel", em_avg_ms)}}}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
