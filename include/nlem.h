@@ -213,6 +213,15 @@ int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch
  */
 int nlem_device_status(nlem_ctx* ctx);
 
+/*
+ * nlem_selftest_timeout - exercises the bounded-wait path on the device: runs the BF16 weight
+ * kernel on a 16 x 16 image with its tensor-core step withheld and a 256-poll bound, so that
+ * every CTA's wait runs out, flags the timeout, frees its TMEM and returns.  Returns what
+ * nlem_device_status then reports: NLEM_ERR_TIMEOUT when the path works (the flag is cleared and
+ * the context stays usable).  Synchronous.
+ */
+int nlem_selftest_timeout(nlem_ctx* ctx);
+
 /* ------------------------------------------------------------------------------------------
  * Learned warm start (not in the paper, which starts from the noisy or the NLM patch and
  * uses one penalty mu for all problems): a 3-layer MLP with FP16 weights and FP32 arithmetic,

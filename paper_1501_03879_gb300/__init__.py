@@ -31,6 +31,7 @@ from ._binding import (  # noqa: F401
     nlem_denoise_ex,
     nlem_denoise_host,
     nlem_device_status,
+    nlem_selftest_timeout,
     nlem_denoise_warm,
     nlem_features,
     nlem_fp32_peak,

@@ -72,6 +72,7 @@ def load_library():
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
         lib.nlem_device_status.argtypes = [vp]
+        lib.nlem_selftest_timeout.argtypes = [vp]
         lib.nlem_bf16_weights.argtypes = [vp, vp, i, i, i, i, i, f, vp, vp]
         lib.nlem_ws_num_params.argtypes = [i]
         lib.nlem_ws_num_params.restype = ll
@@ -376,6 +377,14 @@ def nlem_device_status(ctx: Context | None = None) -> int:
     import torch
     c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
     return _check(load_library().nlem_device_status(c.handle))
+
+
+def nlem_selftest_timeout(ctx: Context | None = None) -> int:
+    """Run the bounded-wait self-test (include/nlem.h) and return its status code: NLEM_ERR_TIMEOUT
+    (-4) when the timeout path works."""
+    import torch
+    c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+    return int(load_library().nlem_selftest_timeout(c.handle))
 
 
 def nlem_bf16_weights(image, patch=9, window=21, h=300.0, ctx: Context | None = None, out=None):

@@ -340,6 +340,37 @@ int nlem_device_status(nlem_ctx* ctx) {
   return NLEM_OK;
 }
 
+int nlem_selftest_timeout(nlem_ctx* ctx) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  rc = nlem_device_status(ctx);   // start from a clean flag
+  if (rc) return rc;
+  if (!ctx->ws_err) {
+    if (cudaMalloc(&ctx->ws_err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(NLEM_ERR_OOM, "status flag could not be allocated");
+    }
+    cudaMemset(ctx->ws_err, 0, sizeof(int));
+  }
+  // a 16 x 16 zero image, 5 x 5 patches, 5 x 5 window: two CTAs, each waiting 256 polls for a
+  // tensor-core commit that is never issued
+  const int n = 16;
+  float* img = nullptr;
+  float* tab = nullptr;
+  if (cudaMalloc(&img, n * n * sizeof(float)) != cudaSuccess || cudaMalloc(&tab, n * n * 25 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(img);
+    return fail(NLEM_ERR_OOM, "self-test buffers could not be allocated");
+  }
+  cudaMemset(img, 0, n * n * sizeof(float));
+  int we = nlemk::launch_bf16_weights(img, n, n, n, 5, 5, 1.f, tab, ctx->ws_err, (cudaStream_t)0, 256u, 0);
+  rc = we ? cuda_fail((cudaError_t)we, "self-test launch") : nlem_device_status(ctx);
+  cudaFree(img);
+  cudaFree(tab);
+  return rc;
+}
+
 int nlem_fp32_peak(nlem_ctx* ctx, double* tflops, int* sm_count) {
   if (!ctx || !tflops) return fail(NLEM_ERR_INVALID, "ctx and tflops must be non-NULL");
   int rc = set_device(ctx);

@@ -23,7 +23,7 @@ namespace {
 constexpr int kBR = 8, kBC = 16, kBM = kBR * kBC;   // pixel block
 constexpr int kN = 256;                             // centres per MMA chunk
 constexpr uint32_t kTmemCols = 256;                 // FP32 accumulator tile 128 x 256
-constexpr uint32_t kWaitTries = 1u << 22;           // bound on mbarrier polls
+constexpr uint32_t kWaitTries = 1u << 22;           // default bound on mbarrier polls
 constexpr int kScrRow = 36;                          // floats per lane of epilogue scratch (16-byte rows,
                                                      // conflict-free 16-byte stores across 8 lanes)
 
@@ -65,8 +65,8 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 }
 
 // Bounded wait for the mbarrier phase with the given parity; false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitTries; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t tries) {
+  for (uint32_t i = 0; i < tries; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -123,7 +123,7 @@ __device__ __forceinline__ float stage_patch(const float* __restrict__ src, int 
 template <int K, int KP>
 __global__ void __launch_bounds__(kBM, 1)
 bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2,
-                    float* __restrict__ wtab, int* __restrict__ err) {
+                    float* __restrict__ wtab, int* __restrict__ err, uint32_t wait_tries, int issue_mma) {
   constexpr int D = K * K, HK = (K - 1) / 2, NKC = KP / 8;   // 16-byte K chunks per row
   constexpr uint32_t SBO = NKC * 128, LBO = 128;
   static_assert(KP % 16 == 0 && KP >= D, "K padding");
@@ -191,7 +191,7 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
-    if (t == 0) {
+    if (t == 0 && issue_mma) {   // issue_mma = 0 only in the timeout self-test: nothing commits
       const uint32_t a0 = smem_u32(Asm), b0 = smem_u32(Bsm);
 #pragma unroll
       for (int kk = 0; kk < KP / 16; ++kk)   // K = 16 per MMA = two 16-byte core matrices
@@ -199,10 +199,14 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
                  kk > 0 ? 1u : 0u);
       mma_commit(&mbar);
     }
-    ok = mbar_wait(&mbar, (uint32_t)(ch & 1));
+    ok = mbar_wait(&mbar, (uint32_t)(ch & 1), wait_tries);
     ok = __syncthreads_and(ok);   // one decision for the whole CTA
     if (!ok) {
+      // flag the timeout, give tensor-core work still in flight one more bounded wait, then
+      // leave the chunk loop to free TMEM
       if (t == 0) atomicExch(err, 1);
+      if (issue_mma) (void)mbar_wait(&mbar, (uint32_t)(ch & 1), wait_tries);
+      __syncthreads();
       break;
     }
     tmem_fence_after_sync();
@@ -245,7 +249,7 @@ bf16_weights_kernel(const float* __restrict__ img, int H, int W, int pitch, int 
 
 template <int K, int KP>
 int launch_weights(const float* img, int H, int W, int pitch, int S, float inv_h2, float* wtab, int* err,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, uint32_t wait_tries, int issue_mma) {
   const int R = (S - 1) / 2;
   const int TR = kBR + 2 * R + (K - 1), TC = kBC + 2 * R + (K - 1);
   const size_t smem = (size_t)kBM * KP * 2 + (size_t)kN * KP * 2 +
@@ -255,19 +259,20 @@ int launch_weights(const float* img, int H, int W, int pitch, int S, float inv_h
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   dim3 grid((W + kBC - 1) / kBC, (H + kBR - 1) / kBR);
-  kern<<<grid, kBM, smem, stream>>>(img, H, W, pitch, S, inv_h2, wtab, err);
+  kern<<<grid, kBM, smem, stream>>>(img, H, W, pitch, S, inv_h2, wtab, err, wait_tries, issue_mma);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
 int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, int S, float inv_h2, float* wtab,
-                        int* err, cudaStream_t stream) {
+                        int* err, cudaStream_t stream, uint32_t wait_tries, int issue_mma) {
+  if (wait_tries == 0) wait_tries = kWaitTries;
   if (S < 1 || S > 31) return -1;   // the compiled range (window <= 31)
   switch (patch) {
-    case 5: return launch_weights<5, 32>(img, H, W, pitch, S, inv_h2, wtab, err, stream);
-    case 7: return launch_weights<7, 64>(img, H, W, pitch, S, inv_h2, wtab, err, stream);
-    case 9: return launch_weights<9, 96>(img, H, W, pitch, S, inv_h2, wtab, err, stream);
+    case 5: return launch_weights<5, 32>(img, H, W, pitch, S, inv_h2, wtab, err, stream, wait_tries, issue_mma);
+    case 7: return launch_weights<7, 64>(img, H, W, pitch, S, inv_h2, wtab, err, stream, wait_tries, issue_mma);
+    case 9: return launch_weights<9, 96>(img, H, W, pitch, S, inv_h2, wtab, err, stream, wait_tries, issue_mma);
     default: return -1;
   }
 }

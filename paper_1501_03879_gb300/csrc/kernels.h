@@ -1,6 +1,7 @@
 // Internal launch descriptors shared by the C-ABI layer and the kernel translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "admm_core.cuh"
 
@@ -53,8 +54,10 @@ struct NlemLaunch {
 
 // BF16 tensor-core cross terms -> weight table wtab [H*W][S*S]; err set to 1 if an MMA wait
 // ran out.  Returns cudaError_t, or -1 for an uncompiled patch size.
+// wait_tries: bound on the mbarrier polls per tensor-core chunk (0 = the default); issue_mma = 0
+// withholds the tensor-core step so that the bounded wait runs out (timeout self-test only).
 int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, int S, float inv_h2, float* wtab,
-                        int* err, cudaStream_t stream);
+                        int* err, cudaStream_t stream, uint32_t wait_tries = 0, int issue_mma = 1);
 
 // Return cudaError_t codes (0 = launched), or -1 when no compiled shape holds the problem.
 int launch_em_batch(const EmLaunch& L);

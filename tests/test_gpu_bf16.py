@@ -75,3 +75,16 @@ def test_bf16_full_size_crop(nl):
     ref = oracle.nlem(g, 9, 21, 300.0, 1.0, 100, weight_mode=1, pixels=pix)["out"]
     assert rel_err(out.reshape(-1)[pix], ref).max() <= TOL
     assert synth.psnr(out, f) > synth.psnr(g, f) + 5
+
+
+def test_bounded_wait_timeout_is_reported(nl):
+    """A tensor-core wait that nothing completes runs out after its bound: the kernel flags it,
+    frees its TMEM and returns; the host reads NLEM_ERR_TIMEOUT, the flag clears and the context
+    keeps working."""
+    assert nl.nlem_selftest_timeout() == -4
+    assert nl.nlem_device_status() == 0
+    g, _ = synth.noisy_image(7200, 24, 24, 30.0)
+    wt = nl.nlem_bf16_weights(torch.from_numpy(g).to(DEV), patch=5, window=5, h=300.0).cpu().numpy()
+    assert nl.nlem_device_status() == 0
+    _, w_model, _ = oracle.nlem_problem(g, 5, 5, 300.0, 24 * 12 + 12, weight_mode=1)
+    assert np.max(np.abs(wt[24 * 12 + 12, :len(w_model)] - w_model)) <= 2e-5 + 2e-5 * np.max(w_model)
