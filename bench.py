@@ -10,10 +10,18 @@ One step = one pass over the production workload:
     [0, 255] with 10% whole-point outliers at 255*Bernoulli(1/2), weights Exp(1), same
     stopping rule.
 Every pixel and every standalone problem is one EM solve; `value` is EM solves per second
-over the whole step (inputs resident in HBM), `mpixel_per_s` the NLEM part alone.
+over the whole step (inputs resident in HBM), `mpixel_per_s` the NLEM part alone.  `e2e` is the
+same step through the public API with host buffers, the copies inside the timed region.
+
+At one GPU the line also carries `extras`, each timed on its own after the main measurement:
+rho = 1e-3 on the same images; the paper's setting (mu = 1e-3, 4 iterations, noisy-patch
+start) with PSNR; BF16 tensor-core weights against FP32 on a 1024x1024 image with impulse
+noise; 64 uneven images in one persistent graph-captured launch; and the learned warm start on
+a 2048x2048 image against plain EM-ADMM.  --no-extras skips them.
 
 --impl reference times the FP64 CPU oracle (the method's plain restatement) on the host
-cores on a bounded sample of the same workload.
+cores on a bounded sample of the same workload.  --profile-case runs the small cases the
+counter captures in profiles/ were taken on.
 """
 from __future__ import annotations
 
