@@ -35,7 +35,8 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 // D_ > 0: compile-time dimension with the tight point layout; D_ == 0: runtime d <= G*Q
 // with a zero-filled full layout.
-template <int D_, int G_, int Q_, int P_, int NW_>
+// MB_ > 0 sets the CTAs per SM the register budget is sized for (default: 2 for 128 threads).
+template <int D_, int G_, int Q_, int P_, int NW_, int MB_ = 0>
 struct Cfg {
   static constexpr int D = D_, G = G_, Q = Q_, P = P_, NW = NW_;
   static constexpr int NT = NW * 32;
@@ -53,7 +54,7 @@ struct Cfg {
   static constexpr int NQR = QR / 4;
   static constexpr int COLS = G * NQR;              // float4 columns of a reduction
   static constexpr int VEC = G * QA;                // slice-layout vectors (z, c, ...)
-  static constexpr int MIN_BLOCKS = (NT <= 128) ? 2 : 1;
+  static constexpr int MIN_BLOCKS = MB_ > 0 ? MB_ : ((NT <= 128) ? 2 : 1);
   static_assert(32 % G == 0, "G must divide the warp");
   static_assert(G <= 4, "a slice must cover at least 8 consecutive lanes");
   static_assert(D == 0 || (QL > 0 && QL <= Q), "bad coordinate split");

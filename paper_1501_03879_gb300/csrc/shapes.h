@@ -7,7 +7,7 @@
 
 namespace nlemk {
 using E49_2 = Cfg<49, 2, 25, 2, 4>;
-using E49_4 = Cfg<49, 2, 25, 4, 4>;
+using E49_4x3 = Cfg<49, 2, 25, 4, 4, 3>;   // three CTAs per SM (168 registers): 5-10% over two
 using E49_7 = Cfg<49, 2, 25, 7, 4>;
 using E49_7W = Cfg<49, 2, 25, 7, 8>;
 using E25_1 = Cfg<25, 1, 25, 1, 4>;
