@@ -124,6 +124,20 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _image(t):
+    """Device pointer and row pitch (elements) of a float32 image [H, W] whose rows are
+    contiguous; row-pitched views (for example a column slice of a wider array) are passed as
+    they are."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("device tensor required (use nlem_denoise_host for host buffers)")
+    if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1) or t.stride(0) < t.shape[1]:
+        raise ValueError("image must be [H, W] with contiguous rows")
+    return ctypes.c_void_p(t.data_ptr()), int(t.stride(0)) if t.shape[0] > 1 else int(t.shape[1])
+
+
 def _need(t, dtype, shape, name):
     import torch
     if t.dtype != dtype:
@@ -259,7 +273,8 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
         obj = torch.empty((H, W), dtype=torch.float64, device=dev)
         kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
     o = _options(tol, check_every, precision, init, fp64_check)
-    _check(load_library().nlem_denoise(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h), float(rho),
+    ip, pitch = _image(image)
+    _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
                                        _ptr(obj), _ptr(kkt), _stream(dev)))
     r = dict(out=o_img, iters_used=used, residual=resid)
@@ -324,11 +339,12 @@ def nlem_denoise_batch(images, patches, windows, hs, rho=1.0, iters=100, box=(0.
         _need(im, torch.float32, tuple(im.shape), f"images[{k}]")
         H, W = im.shape
         d = descs[k]
-        d.image = _ptr(im).value
+        ip, pitch = _image(im)
+        d.image = ip.value
         d.out = _ptr(outs[k]["out"]).value
         d.iters_used = _ptr(outs[k]["iters_used"]).value if outs[k].get("iters_used") is not None else None
         d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
-        d.H, d.W, d.pitch = H, W, W
+        d.H, d.W, d.pitch = H, W, pitch
         d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
     o = _options(tol, check_every, PREC_FP32, init)
     _check(load_library().nlem_denoise_batch(c.handle, descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
@@ -360,11 +376,12 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
         _need(im, torch.float32, tuple(im.shape), f"images[{k}]")
         H, W = im.shape
         d = descs[k]
-        d.image = _ptr(im).value
+        ip, pitch = _image(im)
+        d.image = ip.value
         d.out = _ptr(outs[k]["out"]).value
         d.iters_used = _ptr(outs[k]["iters_used"]).value if outs[k].get("iters_used") is not None else None
         d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
-        d.H, d.W, d.pitch = H, W, W
+        d.H, d.W, d.pitch = H, W, pitch
         d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
     o = _options(tol, check_every, PREC_FP32, init)
     _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
@@ -396,7 +413,8 @@ def nlem_bf16_weights(image, patch=9, window=21, h=300.0, ctx: Context | None = 
     c = ctx or _ctx(image.device)
     if out is None:
         out = torch.full((H * W, window * window), float("nan"), dtype=torch.float32, device=image.device)
-    _check(load_library().nlem_bf16_weights(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+    ip, pitch = _image(image)
+    _check(load_library().nlem_bf16_weights(c.handle, ip, H, W, pitch, int(patch), int(window), float(h),
                                             _ptr(out), _stream(image.device)))
     return out
 
@@ -498,7 +516,8 @@ def nlem_features(image, patch=7, window=21, h=200.0, pixels=None, ctx: Context 
     feats = torch.empty((n, 2 * d + 2), dtype=torch.float32, device=image.device)
     if pixels is not None:
         _need(pixels, torch.int32, (n,), "pixels")
-    _check(load_library().nlem_features(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+    ip, pitch = _image(image)
+    _check(load_library().nlem_features(c.handle, ip, H, W, pitch, int(patch), int(window), float(h),
                                         _ptr(pixels), n, _ptr(feats), _stream(image.device)))
     return feats
 
@@ -530,7 +549,8 @@ def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=
             z = torch.zeros((H * W, d), dtype=torch.float32, device=dev)
     n = pixels.numel() if pixels is not None else 0
     opts = _options(tol, check_every, PREC_FP32, init)
-    _check(load_library().nlem_denoise_ex(c.handle, _ptr(image), H, W, W, int(patch), int(window), float(h), float(rho),
+    ip, pitch = _image(image)
+    _check(load_library().nlem_denoise_ex(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                           int(iters), _Box(*box), ctypes.byref(opts), _ptr(pixels), n, _ptr(x0),
                                           _ptr(rho_pix), _ptr(o), _ptr(used), _ptr(resid), _ptr(z), _stream(dev)))
     r = dict(out=o, iters_used=used, residual=resid)
@@ -557,7 +577,8 @@ def nlem_denoise_warm(ws: WarmStart, image, patch=7, window=21, h=200.0, rho_fal
         used = torch.empty((H, W), dtype=torch.int32, device=dev)
     opts = _options(tol, check_every, PREC_FP32, INIT_WEIGHTED_MEAN)
     fb = ctypes.c_longlong(-1)
-    _check(load_library().nlem_denoise_warm(c.handle, ws.handle, _ptr(image), H, W, W, int(patch), int(window), float(h),
+    ip, pitch = _image(image)
+    _check(load_library().nlem_denoise_warm(c.handle, ws.handle, ip, H, W, pitch, int(patch), int(window), float(h),
                                             float(rho_fallback), int(iters), _Box(*box), ctypes.byref(opts), _ptr(o),
                                             _ptr(used), ctypes.byref(fb) if count_fallback else None, _stream(dev)))
     return dict(out=o, iters_used=used, fallback=int(fb.value) if count_fallback else None)
