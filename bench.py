@@ -380,6 +380,10 @@ def extra_warm_start(nl, ctx, n_train):
     img = torch.from_numpy(g).to(dev)
     kw = dict(patch=7, window=21, h=250.0, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx)
     ms_w, rw = _timed(lambda: nl.nlem_denoise_warm(ws, img, rho_fallback=RHO, **kw))
+    # the learned start's own cost, timed separately: the feature pass and the network
+    ms_f, feats_img = _timed(lambda: nl.nlem_features(img, 7, 21, 250.0, ctx=ctx))
+    ms_m, _ = _timed(lambda: ws.predict(feats_img), reps=3)
+    del feats_img
     ms_p, rp = _timed(lambda: nl.nlem_denoise(img, rho=RHO, **kw), warm=0)
     best_rho = wst.RHO_GRID[int(np.argmax(info["best_rho_counts"]))]
     ms_b, rb = _timed(lambda: nl.nlem_denoise(img, rho=best_rho, **kw), warm=0)
@@ -392,7 +396,8 @@ def extra_warm_start(nl, ctx, n_train):
             "training": {"solves": int(feats.shape[0]), "epochs": 20, "seconds": t_train, "loss_first": hist[0],
                          "loss_last": hist[-1], "label_rho_counts": dict(zip([str(r) for r in info["rho_grid"]],
                                                                              info["best_rho_counts"]))},
-            "warm": {"solves_per_s": npx / (ms_w * 1e-3), "iters_mean": it_w, "fallback_frac": rw["fallback"] / npx},
+            "warm": {"solves_per_s": npx / (ms_w * 1e-3), "iters_mean": it_w, "fallback_frac": rw["fallback"] / npx,
+                     "ms": ms_w, "features_ms": ms_f, "mlp_ms": ms_m, "mlp_share": ms_m / ms_w},
             "plain_rho1": {"solves_per_s": npx / (ms_p * 1e-3), "iters_mean": it_p,
                            "cap_hit": float((rp["iters_used"] >= CAP).float().mean().item())},
             "plain_best_rho": {"rho": best_rho, "solves_per_s": npx / (ms_b * 1e-3), "iters_mean": it_b},
