@@ -37,6 +37,11 @@ extern "C" {
 #define NLEM_INIT_WEIGHTED_MEAN 0   /* z0 = P_C(sum w_j P_j / sum w_j): the NLM patch (Sec. 3) */
 #define NLEM_INIT_NOISY_PATCH 1     /* z0 = P_C(P_i): the noisy patch (Sec. 3) */
 
+#define NLEM_LAYOUT_AUTO 0          /* nlem_denoise picks the problem-to-CTA layout */
+#define NLEM_LAYOUT_PIXEL 1         /* one pixel's problem per CTA */
+#define NLEM_LAYOUT_PAIR 2          /* two horizontally adjacent pixels per CTA, sharing the points
+                                       of their overlapping windows (patch 7, window <= 21) */
+
 typedef struct nlem_ctx nlem_ctx;
 
 /* C = [lo, hi]^d, the box of Sec. 3 (e.g. [0, 255] for 8-bit grayscale). */
@@ -53,7 +58,9 @@ typedef struct {
   int init;           /* NLEM_INIT_* (nlem_denoise only; em_solve_batch uses x0) */
   int fp64_check;     /* != 0: also compute, in FP64 on the GPU, the objective of problem (1)
                          and its optimality residual at the returned point (see outputs) */
-  int reserved[3];
+  int layout;         /* NLEM_LAYOUT_* (nlem_denoise only); PAIR where the pair kernel does not
+                         apply (BF16 precision, other patch sizes, window > 21) is -5 */
+  int reserved[2];
 } nlem_options;
 
 void nlem_options_default(nlem_options* opt);
@@ -121,6 +128,10 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
  * ||P_i||^2 + ||P_j||^2 - 2 <P_i, P_j> are computed from bfloat16-rounded patches on the
  * tensor cores (tcgen05, FP32 accumulation), the norms in FP32, into a context-owned weight
  * table; the ADMM iterations stay in FP32.  Patch 5, 7 or 9.
+ * opt->layout: AUTO runs one pixel per CTA.  PAIR runs the pixel-pair kernel (pixels
+ * (y, 2m) and (y, 2m+1) in one CTA, every shared window point read once for both; patch 7,
+ * FP32, window <= 21); each pixel still stops at its own residual check, so the layouts
+ * differ only by FP32 rounding order.
  * Errors: -1 if patch or window is even or < 1, patch > min(H, W),
  * h <= 0, rho <= 0, iters < 0, lo > hi; -5 if patch*patch > 128 or the window holds more
  * points than the kernels support (window <= 31).

@@ -14,6 +14,9 @@ from __future__ import annotations
 from ._binding import (  # noqa: F401
     INIT_NOISY_PATCH,
     INIT_WEIGHTED_MEAN,
+    LAYOUT_AUTO,
+    LAYOUT_PAIR,
+    LAYOUT_PIXEL,
     PREC_BF16,
     PREC_FP32,
     Context,

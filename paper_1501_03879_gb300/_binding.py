@@ -12,6 +12,9 @@ PREC_FP32 = 0
 PREC_BF16 = 1
 INIT_WEIGHTED_MEAN = 0
 INIT_NOISY_PATCH = 1
+LAYOUT_AUTO = 0
+LAYOUT_PIXEL = 1
+LAYOUT_PAIR = 2
 
 _ERRNAMES = {-1: "NLEM_ERR_INVALID", -2: "NLEM_ERR_CUDA", -3: "NLEM_ERR_OOM", -4: "NLEM_ERR_TIMEOUT",
              -5: "NLEM_ERR_UNSUPPORTED"}
@@ -35,7 +38,8 @@ class _ImageDesc(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
-                ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("layout", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -151,7 +155,8 @@ def _stream(device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False):
+def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False,
+             layout=0):
     o = _Options()
     load_library().nlem_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -159,6 +164,7 @@ def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEA
     o.precision = int(precision)
     o.init = int(init)
     o.fp64_check = 1 if fp64_check else 0
+    o.layout = int(layout)
     return o
 
 
@@ -250,9 +256,10 @@ def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=Non
 
 def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                  precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None,
-                 out=None):
+                 out=None, layout=LAYOUT_AUTO):
     """NLEM (Sec. 3) of a float32 CUDA image [H, W].  Returns dict(out [H,W], iters_used,
-    residual[, obj64, kkt64])."""
+    residual[, obj64, kkt64]).  layout: LAYOUT_AUTO, LAYOUT_PIXEL (one pixel per CTA) or
+    LAYOUT_PAIR (two adjacent pixels per CTA; patch 7, window <= 21, FP32)."""
     import torch
     H, W = image.shape
     _need(image, torch.float32, (H, W), "image")
@@ -272,7 +279,7 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
     if fp64_check:
         obj = torch.empty((H, W), dtype=torch.float64, device=dev)
         kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, precision, init, fp64_check)
+    o = _options(tol, check_every, precision, init, fp64_check, layout)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),

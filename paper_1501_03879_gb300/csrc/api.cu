@@ -52,6 +52,8 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
       return fail(NLEM_ERR_INVALID, "unknown precision %d", opt->precision);
     if (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH)
       return fail(NLEM_ERR_INVALID, "unknown init %d", opt->init);
+    if (opt->layout < NLEM_LAYOUT_AUTO || opt->layout > NLEM_LAYOUT_PAIR)
+      return fail(NLEM_ERR_INVALID, "unknown layout %d", opt->layout);
   }
   return NLEM_OK;
 }
@@ -225,6 +227,7 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   L.n_list = nullptr;
   L.max_items = 0;
   L.ex = nlemk::PixelExtra{};
+  L.layout = opt ? opt->layout : NLEM_LAYOUT_AUTO;
   if (opt && opt->precision == NLEM_PREC_BF16) {
     // cross terms on the tensor cores into the weight table, then the solver reads it
     const size_t need = (size_t)H * W * (size_t)window * window;
@@ -253,6 +256,9 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
     L.wtab = ctx->ws_wtab;
   }
   int e = nlemk::launch_nlem_fp32(L);
+  if (e == -1 && L.layout == NLEM_LAYOUT_PAIR)
+    return fail(NLEM_ERR_UNSUPPORTED, "the pair layout takes FP32, patch 7 and window <= 21 (got patch %d, window %d)",
+                patch, window);
   if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for patch %d, window %d", patch, window);
   if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise launch");
   return NLEM_OK;

@@ -28,6 +28,7 @@ int launch_em_batch(const EmLaunch& L) {
 }
 
 int launch_nlem_fp32(const NlemLaunch& L) {
+  if (L.layout == 2) return launch_nlem_pair_k7(L);
   if (L.patch == 7) return launch_nlem_k7(L);
   if (L.patch == 5) return launch_nlem_k5(L);
   if (L.patch == 9) return launch_nlem_k9(L);

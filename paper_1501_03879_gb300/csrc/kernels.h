@@ -48,6 +48,7 @@ struct NlemLaunch {
   const long long* n_list;
   long long max_items;   // upper bound of *n_list (sizes the grid)
   PixelExtra ex;
+  int layout;            // NLEM_LAYOUT_* of the options (0 = auto)
   int sm_count;
   cudaStream_t stream;
 };
@@ -62,6 +63,9 @@ int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, in
 // Return cudaError_t codes (0 = launched), or -1 when no compiled shape holds the problem.
 int launch_em_batch(const EmLaunch& L);
 int launch_nlem_fp32(const NlemLaunch& L);
+// The pixel-pair kernel (7x7 patches, window <= 21, plain FP32 NLEM over the whole image).
+bool nlem_pair_eligible(const NlemLaunch& L);
+int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
 
