@@ -79,31 +79,45 @@ def rank_workload(rank: int, world: int):
     return {"image_seeds": [SEED * 10 + i + 100 * rank for i in range(len(SIGMAS))], "em_seed": SEED + rank}
 
 
-# Counters of the ncu capture summarised in profiles/nlem_kernel_d49_counters.md, valid only for
-# the kernel sources they were taken on (hash below); any later change of those sources reports
-# null until a new capture is recorded here.  traffic = dram__bytes_read.sum +
-# dram__bytes_write.sum per full launch, scaled from the small case by units processed; the
-# percentages are sm__pipe_fma_cycles_active, smsp__issue_active and the shared-memory
-# wavefronts, each as a fraction of peak over the captured launch.
-KERNEL_SOURCES = ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879_gb300/csrc/solve_kernels.cuh",
-                  "paper_1501_03879_gb300/csrc/shapes.h"]
+# The NLEM step (patch 7, window 21, FP32) runs the pixel-pair kernel; the standalone batch the
+# one-problem-per-CTA kernel.
+NLEM_KERNEL = "nlem_pair_kernel"
+EM_KERNEL = "em_batch_kernel"
+
+# Counters of the ncu captures summarised in profiles/, each valid only for the sources its kernel
+# was built from (hash of the files below); a kernel whose sources changed since reports null
+# until a new capture is recorded.  traffic = dram__bytes_read.sum + dram__bytes_write.sum per
+# full launch, scaled from the small case by units processed; the percentages are
+# sm__pipe_fma_cycles_active, smsp__issue_active and the shared-memory wavefronts, each as a
+# fraction of peak over the captured launch.
+KERNEL_SOURCES = {
+    "nlem_pair_kernel": ["paper_1501_03879_gb300/csrc/nlem_pair.cu", "paper_1501_03879_gb300/csrc/admm_core.cuh"],
+    "nlem_kernel": ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879_gb300/csrc/solve_kernels.cuh",
+                    "paper_1501_03879_gb300/csrc/shapes.h"],
+    "em_batch_kernel": ["paper_1501_03879_gb300/csrc/admm_core.cuh", "paper_1501_03879_gb300/csrc/solve_kernels.cuh",
+                        "paper_1501_03879_gb300/csrc/shapes.h"],
+}
 PROFILED = {
-    "54e40d8b984cc1f2": {
-        "nlem_kernel": {"traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58, "issue_pct": 37.33,
-                        "smem_wavefront_pct": 67.65},
-        "em_batch_kernel": {"traffic": (362509824 + 4014336) * 64, "fma_pipe_pct": 41.33, "issue_pct": 36.46,
-                            "smem_wavefront_pct": 63.73},
-    },
+    "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
+                    "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
+    "em_batch_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (362509824 + 4014336) * 64, "fma_pipe_pct": 41.33,
+                        "issue_pct": 36.46, "smem_wavefront_pct": 63.73},
 }
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(kernel):
     import hashlib
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def profiled_counters():
+    """The recorded counters of every kernel whose sources are unchanged since their capture."""
+    return {k: {m: v for m, v in d.items() if m != "sources"} for k, d in PROFILED.items()
+            if d["sources"] == kernel_sources_hash(k)}
 
 
 def profile_case(which="traffic"):
@@ -552,9 +566,9 @@ def main():
     em_avg_ms = statistics.mean(em_ms)
     nlem_ach = nlem_fl / len(SIGMAS) / (nlem_avg_ms / 1e3) / 1e12
     em_ach = em_fl / (em_avg_ms / 1e3) / 1e12
-    dominant = "nlem_kernel" if sum(nlem_ms) >= sum(em_ms) else "em_batch_kernel"
-    ach = nlem_ach if dominant == "nlem_kernel" else em_ach
-    prof = PROFILED.get(kernel_sources_hash(), {})
+    dominant = NLEM_KERNEL if sum(nlem_ms) >= sum(em_ms) else EM_KERNEL
+    ach = nlem_ach if dominant == NLEM_KERNEL else em_ach
+    prof = profiled_counters()
     traffic = prof.get(dominant, {}).get("traffic")
 
     def dram_gbs(kernel, avg_ms):   # profiled DRAM bytes per launch / the live launch time
@@ -565,11 +579,10 @@ def main():
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_mhz_max:.0f} MHz",
                 "ncu": {k: {m: v for m, v in d.items() if m != "traffic"} for k, d in prof.items()} or None,
                 "fma_chain_measured_tflops": tf_chain,
-                "per_kernel": {"nlem_kernel": {"tflops": nlem_ach, "frac": nlem_ach / peak_alu,
-                                               "avg_ms": nlem_avg_ms, "dram_gbs": dram_gbs("nlem_kernel", nlem_avg_ms)},
-                               "em_batch_kernel": {"tflops": em_ach, "frac": em_ach / peak_alu,
-                                                   "avg_ms": em_avg_ms,
-                                                   "dram_gbs": dram_gbs("em_batch_kernel", em_avg_ms)}}}
+                "per_kernel": {NLEM_KERNEL: {"tflops": nlem_ach, "frac": nlem_ach / peak_alu,
+                                             "avg_ms": nlem_avg_ms, "dram_gbs": dram_gbs(NLEM_KERNEL, nlem_avg_ms)},
+                               EM_KERNEL: {"tflops": em_ach, "frac": em_ach / peak_alu, "avg_ms": em_avg_ms,
+                                           "dram_gbs": dram_gbs(EM_KERNEL, em_avg_ms)}}}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None

@@ -128,10 +128,11 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
  * ||P_i||^2 + ||P_j||^2 - 2 <P_i, P_j> are computed from bfloat16-rounded patches on the
  * tensor cores (tcgen05, FP32 accumulation), the norms in FP32, into a context-owned weight
  * table; the ADMM iterations stay in FP32.  Patch 5, 7 or 9.
- * opt->layout: AUTO runs one pixel per CTA.  PAIR runs the pixel-pair kernel (pixels
- * (y, 2m) and (y, 2m+1) in one CTA, every shared window point read once for both; patch 7,
- * FP32, window <= 21); each pixel still stops at its own residual check, so the layouts
- * differ only by FP32 rounding order.
+ * opt->layout: PAIR runs the pixel-pair kernel (pixels (y, 2m) and (y, 2m+1) in one CTA,
+ * every shared window point read once for both; patch 7, FP32, window <= 21); PIXEL one
+ * pixel per CTA; AUTO takes PAIR for patch 7 in FP32 with window 17..21 and PIXEL otherwise.
+ * Each pixel still stops at its own residual check, so the layouts differ only by FP32
+ * rounding order.
  * Errors: -1 if patch or window is even or < 1, patch > min(H, W),
  * h <= 0, rho <= 0, iters < 0, lo > hi; -5 if patch*patch > 128 or the window holds more
  * points than the kernels support (window <= 31).

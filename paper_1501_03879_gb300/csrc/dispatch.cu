@@ -29,6 +29,9 @@ int launch_em_batch(const EmLaunch& L) {
 
 int launch_nlem_fp32(const NlemLaunch& L) {
   if (L.layout == 2) return launch_nlem_pair_k7(L);
+  // windows of more than 256 points (17x17 and up): the pixel-pair kernel; smaller windows run
+  // the three-CTAs-per-SM pixel shape
+  if (L.layout == 0 && nlem_pair_eligible(L) && L.S * L.S > E49_4x3::CAP) return launch_nlem_pair_k7(L);
   if (L.patch == 7) return launch_nlem_k7(L);
   if (L.patch == 5) return launch_nlem_k5(L);
   if (L.patch == 9) return launch_nlem_k9(L);

@@ -26,7 +26,8 @@
 // 8 warps' columns are summed by warp 0 after one CTA barrier.  Column c of slice g:
 //   c = 0..2  A coordinates 12g + 4c .. +3        c = 4..6  B coordinates 12g + 4(c-4) .. +3
 //   c = 3     (A tail sum, A ||dh||^2, A ||g||^2)  c = 7     (B tail sum, B ||dh||^2, B ||g||^2)
-// z, c = 2z - z_prev, sum g and the centre patches are kept in the same column layout.
+// z, c = 2z - z_prev, sum g and the centre patches are kept in the same column layout, each
+// slice padded to 9 float4 so that the broadcast loads of the 4 slices hit different banks.
 //
 // Each problem stops at its own residual check (or the cap): its z is frozen from then on and
 // the CTA runs until both are frozen, so the result of each pixel is the iterate at which its
@@ -48,17 +49,21 @@ constexpr int DP = 52;                         // point row stride (floats)
 constexpr int EX0 = (P - 1) * NG;              // slot of the first exclusive pair
 constexpr int RMAX = 21;                       // window rows (window <= 21)
 constexpr int NCOL = 32;                       // columns: 4 slices x 8
+constexpr int VQ = 9;                          // float4 per slice in the vector layout: 8 columns
+                                               // and a pad, so the slices sit in different banks
+constexpr int VEC = G * VQ * 4;                // floats per vector (z, c, sum g, centre patches)
 constexpr int TILE_MAX = 1024;                 // tile floats ((21 + 6) x (22 + 6) = 756)
 
 constexpr int OFF_PTS = 0;
 constexpr int OFF_PTSB = OFF_PTS + CAP * DP;
-constexpr int OFF_LAM = OFF_PTSB + RMAX * DP;  // float2 (lam_A, lam_B) per slot
-constexpr int OFF_FLAG = OFF_LAM + 2 * CAP;    // int per slot: bit 0 A's point, bit 1 B's point
+constexpr int OFF_LAM = OFF_PTSB + RMAX * DP;  // float2 (lam_A, lam_B) per slot, at lam_at(j)
+constexpr int SZ_LAM = 2 * (CAP + 2 * P);
+constexpr int OFF_FLAG = OFF_LAM + SZ_LAM;     // int per slot: bit 0 A's point, bit 1 B's point
 constexpr int OFF_ZV = OFF_FLAG + CAP;
-constexpr int OFF_CV = OFF_ZV + 4 * NCOL;
-constexpr int OFF_SGV = OFF_CV + 4 * NCOL;
-constexpr int OFF_PCV = OFF_SGV + 4 * NCOL;
-constexpr int OFF_CRED = OFF_PCV + 4 * NCOL;   // float4 [NW][NCOL]
+constexpr int OFF_CV = OFF_ZV + VEC;
+constexpr int OFF_SGV = OFF_CV + VEC;
+constexpr int OFF_PCV = OFF_SGV + VEC;
+constexpr int OFF_CRED = OFF_PCV + VEC;        // float4 [NW][NCOL]
 constexpr int OFF_TILE = OFF_CRED + 4 * NW * NCOL;   // the tile (setup), FP64 scratch (check)
 constexpr int OFF_SCAL = OFF_TILE + TILE_MAX;
 constexpr int TOTAL = OFF_SCAL + 32;
@@ -71,7 +76,8 @@ static_assert(EX0 + RMAX <= CAP && RMAX <= NG, "exclusive slots sit at point ind
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 // scal: [0] A frozen, [1] B frozen, [2] A iterations, [3] A residual, [4] B iterations,
-// [5] B residual, [8] sum w_A, [9] sum w_B
+// [5] B residual; as int: [6] the next iteration checks the residuals, [7] iterations to the
+// next periodic check
 struct Sm {
   float* pts;
   float* ptsB;
@@ -90,13 +96,31 @@ struct Sm {
         pcv(b + OFF_PCV), cred(reinterpret_cast<float4*>(b + OFF_CRED)), tile(b + OFF_TILE), scal(b + OFF_SCAL) {}
 };
 
+// float2 index of slot j's (lam_A, lam_B): each block of NG slots (one point index p) is shifted
+// by 2 float2, so that the s step's loads of points p and p + 4 fall in different banks
+__host__ __device__ __forceinline__ int lam_at(int j) { return j + 2 * (j / NG); }
+
 // index of coordinate q (0..48) of problem X (0 = A, 1 = B) in the column layout
 __host__ __device__ __forceinline__ int vidx(int q, int X) {
   if (q < 4 * G * NQ) {
     const int g = q / QM, i = q - g * QM;
-    return (g * 8 + 4 * X + i / 4) * 4 + (i % 4);
+    return (g * VQ + 4 * X + i / 4) * 4 + (i % 4);
   }
-  return ((G - 1) * 8 + 4 * X + 3) * 4;
+  return ((G - 1) * VQ + 4 * X + 3) * 4;
+}
+// float4 index of column col (= slice * 8 + c) in the vector layout
+__host__ __device__ __forceinline__ int vcol(int col) { return (col >> 3) * VQ + (col & 7); }
+
+// The check schedule of the stopping rule: iteration `it` evaluates the residuals when it is
+// the cap or, with a tolerance, every check_every-th iteration.  One thread keeps a countdown
+// in shared memory and publishes the flag of iteration next_it, so the others read a flag
+// instead of each computing a remainder.
+__device__ __forceinline__ void schedule_check(float* scal, int next_it, const SolveParams& prm) {
+  int* si = reinterpret_cast<int*>(scal);
+  const int cnt = si[7];
+  const bool periodic = cnt == 1;
+  si[7] = periodic ? prm.check_every : cnt - 1;
+  si[6] = (next_it == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
 }
 
 __device__ __forceinline__ int lane_g() { return (threadIdx.x & 31) >> 3; }
@@ -158,8 +182,8 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
   }
 
   for (int it = 1; it <= prm.iters; ++it) {
-    const bool check = (it == prm.iters) || (prm.tol > 0.f && (it % prm.check_every) == 0);
-    const float4* cv4 = reinterpret_cast<const float4*>(sm.cv) + g * 8;
+    const bool check = reinterpret_cast<const int*>(sm.scal)[6] != 0;
+    const float4* cv4 = reinterpret_cast<const float4*>(sm.cv) + g * VQ;
     // phase 1: e = c + h in place and the squared norms, one problem at a time
     float nA[P], nB[P];
     {
@@ -206,23 +230,52 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
         nB[p] += sq.y;
       }
     }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      nA[p] = gsum(nA[p]);
-      nB[p] = gsum(nB[p]);
-    }
-    // s = min(1, lam / ||e||) (r2 = 0 gives 1 through fminf, harmless since e = 0 there)
+    // s = min(1, lam / ||e||) for the 14 (point, problem) pairs of the group.  The partial norms
+    // are reduce-scattered over the group's 4 lanes (8 apart): after the xor-16 step the lanes
+    // with bit 4 clear hold A's norms, the others B's; after the xor-8 step bit 3 picks points
+    // 0..3 or 4..6.  Each lane turns its own full norms into s (4 rsqrt instead of 14), and the
+    // s values are gathered back.  r2 = 0 gives s = 1 through fminf, harmless since e = 0 there.
     float sA[P], sB[P];
-    float gsA = 0.f, gsB = 0.f;
+    float gsA = 0.f, gsB = 0.f;   // sum of ||g||^2 over the pairs this lane owns
+    {
+      const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+      float v7[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const float2 l = sm.lam[pg + p * NG];
-      sA[p] = fminf(1.f, l.x * rsqrtf(nA[p]));
-      sB[p] = fminf(1.f, l.y * rsqrtf(nB[p]));
-      gsA = fmaf(sA[p] * sA[p], nA[p], gsA);
-      gsB = fmaf(sB[p] * sB[p], nB[p], gsB);
+      for (int p = 0; p < P; ++p) {
+        const float keep = b16 ? nB[p] : nA[p], send = b16 ? nA[p] : nB[p];
+        v7[p] = keep + __shfl_xor_sync(kFull, send, 16);
+      }
+      constexpr int PH = (P + 1) / 2;   // 4: points per half
+      float s4[PH];
+      float gsX = 0.f;
+      const float* lamf = reinterpret_cast<const float*>(sm.lam) + (b16 ? 1 : 0);
+#pragma unroll
+      for (int i = 0; i < PH; ++i) {
+        const float lo = v7[i], hi = PH + i < P ? v7[PH + i] : 0.f;
+        const float keep = b8 ? hi : lo, send = b8 ? lo : hi;
+        const float r2 = keep + __shfl_xor_sync(kFull, send, 8);
+        const int p = (b8 ? PH : 0) + i;
+        const bool valid = p < P;
+        const float l = valid ? lamf[2 * lam_at(pg + p * NG)] : 0.f;
+        s4[i] = valid ? fminf(1.f, l * rsqrtf(r2)) : 0.f;
+        gsX = fmaf(s4[i] * s4[i], valid ? r2 : 0.f, gsX);
+      }
+      float s7[P];
+#pragma unroll
+      for (int i = 0; i < PH; ++i) {
+        const float other = __shfl_xor_sync(kFull, s4[i], 8);
+        s7[i] = b8 ? other : s4[i];
+        if (PH + i < P) s7[PH + i] = b8 ? s4[i] : other;
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float other = __shfl_xor_sync(kFull, s7[p], 16);
+        sA[p] = b16 ? other : s7[p];
+        sB[p] = b16 ? s7[p] : other;
+      }
+      gsA = b16 ? 0.f : gsX;
+      gsB = b16 ? gsX : 0.f;
     }
-    if (g != 0) gsA = gsB = 0.f;   // each point's ||g||^2 once, by its slice-0 lane
     // residual pass (check iterations): ||h(t) - h(t+1)||^2 = ||(1-s) e + a - c||^2
     float ddA = 0.f, ddB = 0.f;
     if (check) {
@@ -263,20 +316,32 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
       const float* abase = sm.pts + pg * DP + g * QM;
       float4 a_n1 = reinterpret_cast<const float4*>(abase)[0];
       float4 a_n2 = reinterpret_cast<const float4*>(abase + NG * DP)[0];
+      float4 a_n3 = reinterpret_cast<const float4*>(abase + 2 * NG * DP)[0];
+      float2 aT = f2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
+      for (int q = 0; q <= NQ; ++q) {   // q = NQ: the tail quad (coordinate 48 and three zeros)
         float2 aA0 = f2(0.f, 0.f), aA1 = aA0, aB0 = aA0, aB1 = aA0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const float4 a4 = a_n1;
           a_n1 = a_n2;
+          a_n2 = a_n3;
           {
-            const int lin = q * P + p + 2;   // the quad two steps ahead
+            const int lin = q * P + p + 3;   // the quad three steps ahead
             const int nq = lin / P, np = lin % P;
-            if (nq < NQ) a_n2 = reinterpret_cast<const float4*>(abase + np * NG * DP)[nq];
+            if (nq < NQ) a_n3 = reinterpret_cast<const float4*>(abase + np * NG * DP)[nq];
+            else if (nq == NQ) a_n3 = tl ? reinterpret_cast<const float4*>(abase + np * NG * DP)[nq]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
           }
           float4 b4 = a4;
-          if (p == P - 1 && pg < nex) b4 = reinterpret_cast<const float4*>(sm.ptsB + pg * DP + g * QM)[q];
+          if (p == P - 1 && pg < nex && (q < NQ || tl))
+            b4 = reinterpret_cast<const float4*>(sm.ptsB + pg * DP + g * QM)[q];
+          if (q == NQ) {
+            const float2 sT = f2(sA[p], sB[p]);
+            aT = __ffma2_rn(sT, hT[p], aT);
+            hT[p] = __ffma2_rn(sT, hT[p], f2(-a4.x, -b4.x));
+            continue;
+          }
           const float2 sA2 = f2(sA[p], sA[p]), sB2 = f2(sB[p], sB[p]);
           aA0 = __ffma2_rn(sA2, hA[p][2 * q], aA0);
           hA[p][2 * q] = __ffma2_rn(sA2, hA[p][2 * q], f2(-a4.x, -a4.y));
@@ -287,17 +352,8 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
           aB1 = __ffma2_rn(sB2, hB[p][2 * q + 1], aB1);
           hB[p][2 * q + 1] = __ffma2_rn(sB2, hB[p][2 * q + 1], f2(-b4.z, -b4.w));
         }
-        u[q] = rs_step(make_float4(aA0.x, aA0.y, aA1.x, aA1.y), make_float4(aB0.x, aB0.y, aB1.x, aB1.y), 4);
-      }
-      float2 aT = f2(0.f, 0.f);
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float* arow = abase + p * NG * DP;
-        const float* brow = brow_of(sm, arow, p, pg, nex);
-        const float2 tv = tl ? f2(arow[QM], brow[QM]) : f2(0.f, 0.f);
-        const float2 sT = f2(sA[p], sB[p]);
-        aT = __ffma2_rn(sT, hT[p], aT);
-        hT[p] = __ffma2_rn(sT, hT[p], f2(-tv.x, -tv.y));
+        if (q < NQ)
+          u[q] = rs_step(make_float4(aA0.x, aA0.y, aA1.x, aA1.y), make_float4(aB0.x, aB0.y, aB1.x, aB1.y), 4);
       }
       u[3] = rs_step(make_float4(aT.x, ddA, gsA, 0.f), make_float4(aT.y, ddB, gsB, 0.f), 4);
     }
@@ -317,48 +373,51 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
       tot = f4add(tot, tb);
       const int c = lane & 7, X = c >> 2, cc = c & 3;
       const bool frozen = sm.scal[X] != 0.f;
+      if (lane == 0) schedule_check(sm.scal, it + 1, prm);
       const float invn = X ? invnB : invnA, fn = X ? fnB : fnA;
       const int nreal = cc < 3 ? 4 : ((lane >> 3) == G - 1 ? 1 : 0);
       float4* zv4 = reinterpret_cast<float4*>(sm.zv);
       float4* cvw = reinterpret_cast<float4*>(sm.cv);
       float4* sgv4 = reinterpret_cast<float4*>(sm.sgv);
-      const float4 z4 = zv4[lane];
+      const int vc = vcol(lane);
+      const float4 z4 = zv4[vc];
       float4 c4o = make_float4(0.f, 0.f, 0.f, 0.f), s4o = c4o;
       if (check) {
-        c4o = cvw[lane];
-        s4o = sgv4[lane];
+        c4o = cvw[vc];
+        s4o = sgv4[vc];
       }
       float p_dd = 0.f, p_dS = 0.f, p_zz = 0.f, p_zx = 0.f, p_dz = 0.f, p_dzA = 0.f, p_E = 0.f, p_G = 0.f;
       float zn[4], cn[4], sn[4];
+      // branch-free: slots that hold no coordinate (z = c = sum g = 0 there) are masked to zero
+      // by selects, which keeps the lane-dependent slot count from splitting the warp
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float A = f4get(tot, i), z = f4get(z4, i);
-        zn[i] = cn[i] = sn[i] = 0.f;
-        if (i < nreal) {
-          const float znew = frozen ? z : clampf(fmaf(-A, invn, z), prm.lo, prm.hi);
-          if (check) {
-            const float del = f4get(c4o, i) - znew;   // c(t) - z(t+1)
-            const float SD = f4get(s4o, i) - A;       // sum_k (g_k(t) - g_k(t+1))
-            const float dz = z - znew;
-            p_dd = fmaf(del, del, p_dd);
-            p_dS = fmaf(del, SD, p_dS);
-            p_zz = fmaf(znew, znew, p_zz);
-            p_zx = fmaf(znew, fmaf(fn, del, SD), p_zx);
-            p_dz = fmaf(dz, dz, p_dz);
-            p_dzA = fmaf(dz, A, p_dzA);
-          }
-          zn[i] = znew;
-          cn[i] = frozen ? z : 2.f * znew - z;
-          sn[i] = A;
+        const bool real = i < nreal;
+        const float A = real ? f4get(tot, i) : 0.f, z = f4get(z4, i);
+        const float zc = frozen ? z : clampf(fmaf(-A, invn, z), prm.lo, prm.hi);
+        const float znew = real ? zc : 0.f;
+        if (check) {
+          const float del = f4get(c4o, i) - znew;   // c(t) - z(t+1)
+          const float SD = f4get(s4o, i) - A;       // sum_k (g_k(t) - g_k(t+1))
+          const float dz = z - znew;
+          p_dd = fmaf(del, del, p_dd);
+          p_dS = fmaf(del, SD, p_dS);
+          p_zz = fmaf(znew, znew, p_zz);
+          p_zx = fmaf(znew, fmaf(fn, del, SD), p_zx);
+          p_dz = fmaf(dz, dz, p_dz);
+          p_dzA = fmaf(dz, A, p_dzA);
         }
+        zn[i] = znew;
+        cn[i] = real ? (frozen ? z : 2.f * znew - z) : 0.f;
+        sn[i] = A;
       }
       if (cc == 3) {
         p_E = tot.y;
         p_G = tot.z;
       }
-      zv4[lane] = make_float4(zn[0], zn[1], zn[2], zn[3]);
-      cvw[lane] = make_float4(cn[0], cn[1], cn[2], cn[3]);
-      sgv4[lane] = make_float4(sn[0], sn[1], sn[2], sn[3]);
+      zv4[vc] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+      cvw[vc] = make_float4(cn[0], cn[1], cn[2], cn[3]);
+      sgv4[vc] = make_float4(sn[0], sn[1], sn[2], sn[3]);
       if (check) {
         // sums over the 16 lanes of the same problem (lane bit 2 = X)
 #pragma unroll
@@ -513,6 +572,8 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
     sm.scal[0] = 0.f;
     sm.scal[1] = hasB ? 0.f : 1.f;
     for (int i = 2; i < 6; ++i) sm.scal[i] = 0.f;
+    reinterpret_cast<int*>(sm.scal)[7] = prm.check_every;
+    schedule_check(sm.scal, 1, prm);
   }
   __syncthreads();
   // point rows: shared positions fill the slots in row-major order, skipping the exclusive
@@ -561,13 +622,13 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
     const int q = cc < 3 ? sg * QM + 4 * cc + slot : ((sg == G - 1 && slot == 0) ? 4 * G * NQ : -1);
     float v = 0.f;
     if (q >= 0 && (X == 0 || hasB)) v = sm.tile[(y - r0 + q / K) * TC + (x + X - a0 + q % K)];
-    sm.pcv[i] = v;
+    sm.pcv[vcol(col) * 4 + slot] = v;
   }
   __syncthreads();
   // weights w_j = exp(-||P_X - P_j||^2 / h^2) of both problems (zero where X has no point j)
   float wA[P], wB[P];
   {
-    const float4* pc4 = reinterpret_cast<const float4*>(sm.pcv) + g * 8;
+    const float4* pc4 = reinterpret_cast<const float4*>(sm.pcv) + g * VQ;
     const float2 pT = tl ? f2(sm.pcv[vidx(48, 0)], sm.pcv[vidx(48, 1)]) : f2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -597,7 +658,7 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
       const int fl = sm.flag[j];
       wA[p] = (fl & 1) ? expf(-dA * inv_h2) : 0.f;
       wB[p] = (fl & 2) ? expf(-dB * inv_h2) : 0.f;
-      if (g == 0) sm.lam[j] = f2(wA[p] * prm.inv_mu, wB[p] * prm.inv_mu);
+      if (g == 0) sm.lam[lam_at(j)] = f2(wA[p] * prm.inv_mu, wB[p] * prm.inv_mu);
     }
   }
   float4* zv4 = reinterpret_cast<float4*>(sm.zv);
@@ -605,13 +666,13 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
   float4* sgv4 = reinterpret_cast<float4*>(sm.sgv);
   if (init_mode == 1) {   // the noisy patches, projected onto C
     if (t < NCOL) {
-      const float4 pc = reinterpret_cast<const float4*>(sm.pcv)[t];
+      const float4 pc = reinterpret_cast<const float4*>(sm.pcv)[vcol(t)];
       const int cc = t & 3, nreal = cc < 3 ? 4 : ((t >> 3) == G - 1 ? 1 : 0);
       float zz[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) zz[i] = i < nreal ? clampf(f4get(pc, i), prm.lo, prm.hi) : 0.f;
-      zv4[t] = cvw[t] = make_float4(zz[0], zz[1], zz[2], zz[3]);
-      sgv4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      zv4[vcol(t)] = cvw[vcol(t)] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+      sgv4[vcol(t)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
   } else {   // P_C(weighted mean) of each problem (sum w >= 1: the centre point weighs 1)
@@ -662,8 +723,8 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
       float zz[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) zz[i] = i < nreal ? clampf(f4get(tot, i) * inv, prm.lo, prm.hi) : 0.f;
-      zv4[lane] = cvw[lane] = make_float4(zz[0], zz[1], zz[2], zz[3]);
-      sgv4[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      zv4[vcol(lane)] = cvw[vcol(lane)] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+      sgv4[vcol(lane)] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
   }
