@@ -106,12 +106,31 @@ int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, in
  *            the projected-gradient optimality residual ||z - P_C(z - g/sum w)||, both in FP64.
  * Errors as em_solve; -5 if n exceeds the largest problem the on-chip (register + shared
  * memory) kernels hold for this d: 896 points for d = 25 and 49, 448 for d = 81, and for other
- * d <= 28 / 60 / 120: 512 / 256 / 256.
+ * d <= 28 / 60 / 120: 512 / 256 / 256.  B == 0 returns 0 at once (the buffers may then be NULL).
  */
 int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n,
                    int d, nlem_box box, float rho, int iters, const float* x0,
                    const nlem_options* opt, float* x_out, int* iters_used, float* residual,
                    double* obj64, double* kkt64, void* stream);
+
+/*
+ * em_solve_batch_host - em_solve_batch on HOST buffers, with the copies pipelined against the
+ * solves.  The batch runs in chunks of `chunk` problems (0 = about 1 GiB of points per chunk).
+ * Chunk k+1's inputs are copied to the device on a context-owned copy stream while chunk k is
+ * solved on `stream`; each chunk's results are copied back on `stream` after its solve.  Two
+ * device chunks are double-buffered in the context workspace.  Waits for completion.
+ *   points_host [B][n][d], weights_host [B][n] float32 (host memory; pinned memory lets the
+ *   copies overlap the solves, pageable memory works without overlap)
+ *   x0_host [B][d] or NULL;  x_out_host [B][d];  iters_used_host [B] int32 or NULL;
+ *   residual_host [B] float32 or NULL: as em_solve_batch.  The FP64 check outputs are not
+ *   returned here (use em_solve_batch).
+ * Errors as em_solve_batch; -1 also for chunk < 0; -3 if the chunk workspace cannot be allocated.
+ * B == 0 returns 0 at once (the buffers may then be NULL), as em_solve_batch does.
+ */
+int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* weights_host, long long B,
+                        int n, int d, nlem_box box, float rho, int iters, const float* x0_host,
+                        const nlem_options* opt, long long chunk, float* x_out_host,
+                        int* iters_used_host, float* residual_host, void* stream);
 
 /*
  * nlem_denoise - NLEM of Sec. 3 (Eq. L1regression) on one grayscale image.

@@ -24,6 +24,7 @@ from ._binding import (  # noqa: F401
     NlemError,
     em_solve,
     em_solve_batch,
+    em_solve_batch_host,
     lib_path,
     load_library,
     nlem_batch_config,

@@ -72,6 +72,8 @@ def load_library():
         lib.nlem_denoise.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp, vp,
                                      vp, vp]
         lib.nlem_denoise_host.argtypes = [vp, vp, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.em_solve_batch_host.argtypes = [vp, vp, vp, ll, i, i, _Box, f, i, vp, ctypes.POINTER(_Options), ll, vp,
+                                            vp, vp, vp]
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
@@ -98,7 +100,8 @@ def load_library():
                                           ctypes.POINTER(ll), vp]
         lib.nlem_denoise_batch_noalloc.argtypes = [ctypes.POINTER(_ImageDesc), i, f, i, _Box,
                                                    ctypes.POINTER(_Options), vp]
-        for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "nlem_denoise",
+        for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "em_solve_batch_host",
+                     "nlem_denoise",
                      "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc",
                      "nlem_device_status", "nlem_bf16_weights", "nlem_ws_create", "nlem_ws_destroy",
                      "nlem_ws_get_params", "nlem_ws_set_params", "nlem_ws_save", "nlem_ws_load", "nlem_ws_forward",
@@ -252,6 +255,50 @@ def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=Non
     if fp64_check:
         r.update(obj64=obj, kkt64=kkt)
     return r
+
+
+def _host_ptr(t, dtype, shape, name):
+    """Pointer of a contiguous CPU tensor (pinned memory lets the library overlap its copies)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a CPU torch.Tensor")
+    _need(t, dtype, shape, name)
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
+                        chunk=0, ctx: Context | None = None, out=None, device=0):
+    """Algorithm 1 on B problems held in HOST memory: points [B, n, d] and weights [B, n] (CPU float32
+    tensors, ideally pinned).  The library copies them in chunks of `chunk` problems (0 = about 1 GiB),
+    overlapping the copy of each chunk with the solve of the previous one, and copies the results
+    back.  Returns dict(x [B,d], iters_used [B] int32, residual [B]) as CPU tensors."""
+    import torch
+    B, n, d = points.shape
+    pp = _host_ptr(points, torch.float32, (B, n, d), "points")
+    wp = _host_ptr(weights, torch.float32, (B, n), "weights")
+    x0p = _host_ptr(x0, torch.float32, (B, d), "x0") if x0 is not None else None
+    c = ctx or _ctx(torch.device("cuda", device))
+    pin = points.is_pinned()
+    res = out or {}
+    x = res.get("x")
+    if x is None:
+        x = torch.empty((B, d), dtype=torch.float32, pin_memory=pin)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty(B, dtype=torch.int32, pin_memory=pin)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.empty(B, dtype=torch.float32, pin_memory=pin)
+    o = _options(tol, check_every)
+    _check(load_library().em_solve_batch_host(c.handle, pp, wp, B, n, d, _Box(*box), float(rho), int(iters), x0p,
+                                              ctypes.byref(o), int(chunk),
+                                              _host_ptr(x, torch.float32, (B, d), "x"),
+                                              _host_ptr(used, torch.int32, (B,), "iters_used"),
+                                              _host_ptr(resid, torch.float32, (B,), "residual"),
+                                              _stream(torch.device("cuda", c.device))))
+    return dict(x=x, iters_used=used, residual=resid)
 
 
 def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,

@@ -136,6 +136,13 @@ int nlem_ctx_destroy(nlem_ctx* ctx) {
   cudaFree(ctx->ws_rho);
   cudaFree(ctx->ws_list);
   cudaFree(ctx->ws_count);
+  cudaFree(ctx->ws_em);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+    if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+  }
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
   return NLEM_OK;
 }
@@ -149,8 +156,8 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
   if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
+  if (B == 0) return NLEM_OK;   // an empty batch may pass NULL buffers
   if (!points || !weights || !x_out) return fail(NLEM_ERR_INVALID, "points, weights and x_out must be non-NULL");
-  if (B == 0) return NLEM_OK;
   if (d > 120 || n > nlemk::em_capacity(d))
     return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d, d <= 120)", n,
                 d, nlemk::em_capacity(d));
@@ -181,6 +188,99 @@ int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, in
              int iters, float* x_out, void* stream) {
   return em_solve_batch(ctx, points, weights, 1, n, d, box, rho, iters, nullptr, nullptr, x_out, nullptr, nullptr,
                         nullptr, nullptr, stream);
+}
+
+int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* weights_host, long long B, int n,
+                        int d, nlem_box box, float rho, int iters, const float* x0_host, const nlem_options* opt,
+                        long long chunk, float* x_out_host, int* iters_used_host, float* residual_host,
+                        void* stream) {
+  int rc = check_common(ctx, box, rho, iters, opt);
+  if (rc) return rc;
+  if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
+  if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
+  if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
+  if (chunk < 0) return fail(NLEM_ERR_INVALID, "chunk must be >= 0 (got %lld)", chunk);
+  if (B == 0) return NLEM_OK;   // an empty batch may pass NULL buffers
+  if (!points_host || !weights_host || !x_out_host)
+    return fail(NLEM_ERR_INVALID, "points_host, weights_host and x_out_host must be non-NULL");
+  if (d > 120 || n > nlemk::em_capacity(d))
+    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d, d <= 120)", n,
+                d, nlemk::em_capacity(d));
+  if ((rc = set_device(ctx))) return rc;
+  const size_t pb = (size_t)n * d * sizeof(float);   // one problem's points
+  long long Bc = chunk > 0 ? chunk : (long long)std::max<size_t>(1, ((size_t)1 << 30) / pb);
+  if (Bc > B) Bc = B;
+  // one chunk buffer: points, weights, start points, results; regions 256-byte aligned
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_w = al((size_t)Bc * pb);
+  const size_t o_x0 = o_w + al((size_t)Bc * n * 4);
+  const size_t o_x = o_x0 + (x0_host ? al((size_t)Bc * d * 4) : 0);
+  const size_t o_it = o_x + al((size_t)Bc * d * 4);
+  const size_t o_res = o_it + al((size_t)Bc * 4);
+  const size_t per = o_res + al((size_t)Bc * 4);
+  if (2 * per > ctx->ws_em_bytes) {
+    // every call waits for its streams before returning, so the old buffers are idle
+    cudaFree(ctx->ws_em);
+    ctx->ws_em = nullptr;
+    ctx->ws_em_bytes = 0;
+    if (cudaMalloc(&ctx->ws_em, 2 * per) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(NLEM_ERR_OOM, "chunk workspace of %zu bytes could not be allocated", 2 * per);
+    }
+    ctx->ws_em_bytes = 2 * per;
+  }
+  if (!ctx->copy_stream) {
+    cudaError_t ce = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+      ce = cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming);
+    }
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return cuda_fail(ce, "copy stream and events of em_solve_batch_host");
+  }
+  cudaStream_t s = (cudaStream_t)stream, cs = ctx->copy_stream;
+  // the copies start after the work already queued on the caller's stream
+  cudaError_t e = cudaEventRecord(ctx->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_start, 0);
+  const long long nchunks = (B + Bc - 1) / Bc;
+  for (long long k = 0; k < nchunks && e == cudaSuccess && rc == NLEM_OK; ++k) {
+    const int b = (int)(k & 1);
+    const long long off = k * Bc, cnt = std::min(Bc, B - off);
+    char* base = ctx->ws_em + b * per;
+    float* dp = reinterpret_cast<float*>(base);
+    float* dw = reinterpret_cast<float*>(base + o_w);
+    float* dx0 = x0_host ? reinterpret_cast<float*>(base + o_x0) : nullptr;
+    float* dx = reinterpret_cast<float*>(base + o_x);
+    int* dit = reinterpret_cast<int*>(base + o_it);
+    float* dres = reinterpret_cast<float*>(base + o_res);
+    // buffer b is free once chunk k-2's solve and read-back on the caller's stream are done
+    if (k >= 2) e = cudaStreamWaitEvent(cs, ctx->ev_done[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, points_host + off * n * d, (size_t)cnt * pb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dw, weights_host + off * n, (size_t)cnt * n * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && x0_host)
+      e = cudaMemcpyAsync(dx0, x0_host + off * d, (size_t)cnt * d * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[b], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_copied[b], 0);
+    if (e != cudaSuccess) break;
+    rc = em_solve_batch(ctx, dp, dw, cnt, n, d, box, rho, iters, dx0, opt, dx, iters_used_host ? dit : nullptr,
+                        residual_host ? dres : nullptr, nullptr, nullptr, stream);
+    if (rc != NLEM_OK) break;
+    e = cudaMemcpyAsync(x_out_host + off * d, dx, (size_t)cnt * d * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && iters_used_host)
+      e = cudaMemcpyAsync(iters_used_host + off, dit, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && residual_host)
+      e = cudaMemcpyAsync(residual_host + off, dres, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done[b], s);
+  }
+  // wait for both streams, on an error too, so that no copy into the workspace is left in flight
+  const cudaError_t ec = cudaStreamSynchronize(cs);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (rc != NLEM_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "em_solve_batch_host copies");
+  if (ec != cudaSuccess) return cuda_fail(ec, "em_solve_batch_host copy stream");
+  if (es != cudaSuccess) return cuda_fail(es, "em_solve_batch_host");
+  return NLEM_OK;
 }
 
 int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,

@@ -22,6 +22,14 @@ struct BatchPlan {
 struct nlem_ctx {
   int device = 0;
   int sm_count = 0;
+  // double-buffered chunks of the pipelined host-buffer batch solve (grown on demand), the copy
+  // stream that fills them, and the events that order buffer reuse
+  char* ws_em = nullptr;
+  size_t ws_em_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
   // workspace for the host-buffer entry point (grown on demand, freed by destroy)
   float* ws_img = nullptr;
   float* ws_out = nullptr;
