@@ -100,12 +100,12 @@ KERNEL_SOURCES = {
                         "paper_1501_03879_gb300/csrc/shapes.h"],
 }
 PROFILED = {
-    "nlem_pair_kernel": {"sources": "d1afa98e8611c786", "traffic": (133120 + 0) * 16, "fma_pipe_pct": 47.81,
+    "nlem_pair_kernel": {"sources": "429400d1bb3111d2", "traffic": (132352 + 0) * 16, "fma_pipe_pct": 47.81,
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.12},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (362509824 + 4014336) * 64, "fma_pipe_pct": 41.33,
-                        "issue_pct": 36.46, "smem_wavefront_pct": 63.73},
+    "em_batch_kernel": {"sources": "91ce3712a71ef8dc", "traffic": (361667072 + 4059136) * 64, "fma_pipe_pct": 41.57,
+                        "issue_pct": 35.43, "smem_wavefront_pct": 66.78},
 }
 
 

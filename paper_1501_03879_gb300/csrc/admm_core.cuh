@@ -329,8 +329,18 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 
   int it = 0;
   float resid = 0.f;
+  // the check schedule (the cap, and every check_every-th iteration with a tolerance): thread 0
+  // keeps a countdown in shared memory and publishes each next iteration's flag, so the other
+  // threads read a flag instead of each computing a remainder
+  int* si = reinterpret_cast<int*>(sm.scal);
+  if (t == 0) {
+    const bool periodic = prm.check_every == 1;
+    si[7] = periodic ? prm.check_every : prm.check_every - 1;
+    si[6] = (1 == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
+  }
+  __syncthreads();
   for (it = 1; it <= prm.iters; ++it) {
-    const bool check = (it == prm.iters) || (prm.tol > 0.f && (it % prm.check_every) == 0);
+    const bool check = si[6] != 0;
     // phase 1: e = c + h (in place) and squared norms, one float4 of c at a time; the
     // points are innermost so that consecutive FFMA2s feed different norm accumulators
     float s[C::P];
@@ -365,18 +375,42 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 #pragma unroll
       for (int p = 0; p < C::P; ++p) s[p] = s2[p].x + s2[p].y;
     }
-#pragma unroll
-    for (int p = 0; p < C::P; ++p) s[p] = point_sum<C>(s[p]);
+    // s = min(1, lam / ||e||); r2 = 0 gives lam*inf (or NaN when lam = 0), and fminf then
+    // yields 1, which is harmless because e = 0 there.
     float gs = 0.f;
+    if constexpr (C::G == 2) {
+      // the two lanes of a point split the points: a reduce-scatter of the partial norms leaves
+      // lane g with the full norm of points 2k+g, which it alone turns into s; the s values are
+      // then exchanged (4 rsqrt per lane instead of 7)
+      constexpr int PH = (C::P + 1) / 2;
+      const bool up = g != 0;
+      float sh[PH];
 #pragma unroll
-    for (int p = 0; p < C::P; ++p) {
-      const float r2 = s[p];
-      // s = min(1, lam / ||e||); r2 = 0 gives lam*inf (or NaN when lam = 0), and fminf
-      // then yields 1, which is harmless because e = 0 there.
-      s[p] = fminf(1.f, sm.lam[pg + p * C::NG] * rsqrtf(r2));
-      gs = fmaf(s[p] * s[p], r2, gs);
+      for (int k = 0; k < PH; ++k) {
+        const float lo = s[2 * k], hi = 2 * k + 1 < C::P ? s[2 * k + 1] : 0.f;
+        const float r2 = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, C::LPG);
+        const int p = 2 * k + (up ? 1 : 0);
+        const bool valid = p < C::P;
+        sh[k] = valid ? fminf(1.f, sm.lam[pg + (valid ? p : 0) * C::NG] * rsqrtf(r2)) : 0.f;
+        gs = fmaf(sh[k] * sh[k], valid ? r2 : 0.f, gs);   // each point's ||g_k||^2 once, by its owner
+      }
+#pragma unroll
+      for (int k = 0; k < PH; ++k) {
+        const float other = __shfl_xor_sync(kFull, sh[k], C::LPG);
+        s[2 * k] = up ? other : sh[k];
+        if (2 * k + 1 < C::P) s[2 * k + 1] = up ? sh[k] : other;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) s[p] = point_sum<C>(s[p]);
+#pragma unroll
+      for (int p = 0; p < C::P; ++p) {
+        const float r2 = s[p];
+        s[p] = fminf(1.f, sm.lam[pg + p * C::NG] * rsqrtf(r2));
+        gs = fmaf(s[p] * s[p], r2, gs);
+      }
+      if (g != 0) gs = 0.f;    // each point's ||g_k||^2 counted once, by its slice-0 lane
     }
-    if (g != 0) gs = 0.f;      // each point's ||g_k||^2 counted once, by its slice-0 lane
     float dd = 0.f;            // sum_k ||h_k(t) - h_k(t+1)||^2 over this lane's slots
     if (check) {
       // ||(1-s) e + a - c||^2 in a pass of its own; the fences keep the compiler from
@@ -471,6 +505,12 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     block_reduce_rows<C>(sm, t0, t1);
     // finalize (warp 0): z+ = P_C(z - sum g / n), c+ = 2 z+ - z, residuals on checks
     if (t < 32) {
+      if (t == 0) {   // the next iteration's check flag (read by every thread after the barrier)
+        const int cnt = si[7];
+        const bool periodic = cnt == 1;
+        si[7] = periodic ? prm.check_every : cnt - 1;
+        si[6] = (it + 1 == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
+      }
       float p_dd = 0.f, p_dS = 0.f, p_zz = 0.f, p_zx = 0.f, p_dz = 0.f, p_dzA = 0.f, p_E = 0.f, p_G = 0.f;
 #pragma unroll
       for (int h2 = 0; h2 < 2; ++h2) {

@@ -144,3 +144,17 @@ def test_pair_layout_rejects_what_it_does_not_cover(nl):
     with pytest.raises(nl.NlemError) as e:
         nl.nlem_denoise(g, patch=7, window=21, iters=2, layout=7)
     assert e.value.code == -1
+
+
+def test_pair_layout_pitched_view_matches_contiguous(nl):
+    """The pair kernel reads the image through its row pitch: a column slice of a wider array
+    gives bitwise the result of its contiguous copy (odd width, window 21)."""
+    g, _ = synth.noisy_image(3601, 30, 37, 20.0)
+    wide = torch.zeros((30, 37 + 11), dtype=torch.float32, device=DEV)
+    wide[:, 3:40] = _t(g)
+    view = wide[:, 3:40]
+    assert not view.is_contiguous()
+    kw = dict(patch=7, window=21, h=200.0, rho=1.0, iters=25, layout=nl.LAYOUT_PAIR)
+    a = nl.nlem_denoise(view, **kw)
+    b = nl.nlem_denoise(view.contiguous(), **kw)
+    assert torch.equal(a["out"], b["out"]) and torch.equal(a["iters_used"], b["iters_used"])
