@@ -303,13 +303,17 @@ int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long 
                     float* x0, float* rho, void* stream);
 
 /* Features f (above) of the NLEM problems of the listed pixels (device linear indices, NULL =
- * all H*W in row-major order) into feats [npix or H*W][2d+2].  window^2 <= 512. */
+ * all H*W in row-major order) into feats [npix or H*W][2d+2].  Patch 5, 7 or 9 and
+ * (window + patch - 1)^2 <= 1024 (the pixel's tile is sorted in one 1024-entry sort); a listed
+ * index outside [0, H*W) gives a row of NaN.  Errors: -1 as nlem_denoise, or npix < 0 with a
+ * list; -5 otherwise unsupported. */
 int nlem_features(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
                   const int* pixels, long long npix, float* feats, void* stream);
 
 /* nlem_denoise on the listed pixels only (NULL = all), optionally from per-pixel start points
  * x0 [pixel][d] and penalties rho_pix [pixel] (device, indexed by linear pixel), writing the
- * centre pixel to out[pixel] and optionally the whole solution patch to z_out [pixel][d]. */
+ * centre pixel to out[pixel] and optionally the whole solution patch to z_out [pixel][d].
+ * A listed index outside [0, H*W) is skipped. */
 int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
                     float rho, int iters, nlem_box box, const nlem_options* opt, const int* pixels, long long npix,
                     const float* x0, const float* rho_pix, float* out, int* iters_used, float* residual,

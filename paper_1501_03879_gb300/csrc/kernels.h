@@ -28,7 +28,6 @@ struct PixelExtra {
   const float* x0;      // [pixel][d] start points (projected onto C), or NULL
   const float* rho;     // [pixel] penalties, or NULL for the launch's rho
   float* z_out;         // [pixel][d] full solution patch, or NULL
-  float* feats;         // [pixel][2d+2] warm-start features; when set, no solve is run
 };
 
 struct NlemLaunch {
@@ -68,6 +67,11 @@ bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
+
+// Warm-start features [item][2 patch^2 + 2] of the listed pixels (or all pixels, row-major);
+// returns cudaError_t, or -1 for an uncompiled patch or a tile larger than 32 x 32.
+int launch_features(const float* img, int H, int W, int pitch, int patch, int S, float inv_h2, const int* pix_list,
+                    const long long* n_list, long long max_items, float* feats, int sm_count, cudaStream_t stream);
 
 // Sets the calling thread's message returned by nlem_last_error().
 void set_last_error(const char* msg);

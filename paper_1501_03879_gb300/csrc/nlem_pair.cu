@@ -768,7 +768,7 @@ nlem_pair_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, 
 
 bool nlem_pair_eligible(const NlemLaunch& L) {
   return L.patch == pairk::K && L.S >= 1 && L.S <= 2 * ((pairk::RMAX - 1) / 2) + 1 && !L.wtab && !L.pix_list &&
-         !L.ex.x0 && !L.ex.rho && !L.ex.z_out && !L.ex.feats;
+         !L.ex.x0 && !L.ex.rho && !L.ex.z_out;
 }
 
 int launch_nlem_pair_k7(const NlemLaunch& L) {

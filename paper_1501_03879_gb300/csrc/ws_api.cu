@@ -387,22 +387,23 @@ int nlem_features(nlem_ctx* ctx, const float* image, int H, int W, int pitch, in
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (!feats) return wfail(NLEM_ERR_INVALID, "feats is NULL");
+  if (pixels && npix < 0) return wfail(NLEM_ERR_INVALID, "npix must be >= 0");
   if ((window + patch - 1) * (window + patch - 1) > 1024)
     return wfail(NLEM_ERR_UNSUPPORTED, "features need (window + patch - 1)^2 <= 1024");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  nlemk::NlemLaunch L = base_launch(ctx, image, H, W, pitch, patch, window, h, 1.f, 0, nlem_box{0.f, 255.f},
-                                    nullptr, s);
   if ((rc = ensure_counts(ctx))) return rc;
+  const long long* n_list = nullptr;
   if (pixels) {
     long long n = npix;
     cudaMemcpyAsync(ctx->ws_count + 1, &n, sizeof(long long), cudaMemcpyHostToDevice, s);
-    L.pix_list = pixels;
-    L.n_list = ctx->ws_count + 1;
-    L.max_items = npix;
+    n_list = ctx->ws_count + 1;
   }
-  L.ex.feats = feats;   // rho = 1 above, so the weights sit unscaled in shared memory
-  return run_launch(L, "features");
+  const int e = nlemk::launch_features(image, H, W, pitch, patch, window, 1.f / (h * h), pixels, n_list, npix, feats,
+                                       ctx->sm_count, s);
+  if (e == -1) return wfail(NLEM_ERR_UNSUPPORTED, "features: patch %d not compiled (5, 7, 9 are)", patch);
+  if (e != 0) return wfail(NLEM_ERR_CUDA, "features launch: %s", cudaGetErrorString((cudaError_t)e));
+  return NLEM_OK;
 }
 
 int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,

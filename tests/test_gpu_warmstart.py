@@ -53,6 +53,42 @@ def test_features_match_oracle(nl):
                 assert abs(cum_at - 0.5 * w.sum()) <= 1e-5 * w.sum(), (lin, c)
 
 
+@pytest.mark.parametrize("k,S", [(5, 15), (9, 21), (7, 25)])
+def test_features_other_patches_and_windows(nl, k, S):
+    """Patch 5 and 9 and the largest 7x7 window (a 31 x 31 tile): the same checks as above."""
+    g, _ = synth.noisy_image(8100 + k + S, 36, 33, 25.0)
+    h = 250.0
+    d = k * k
+    pix = np.array([0, 32, 33 * 18 + 17, 36 * 33 - 1, 33 * 5 + 30], dtype=np.int32)
+    feats = nl.nlem_features(torch.from_numpy(g).to(DEV), k, S, h, pixels=torch.from_numpy(pix).to(DEV)).cpu().numpy()
+    for row, lin in zip(feats, pix):
+        pts, w, _ = oracle.nlem_problem(g, k, S, h, int(lin))
+        f = oracle.features(pts, w.astype(np.float32).astype(np.float64))
+        assert rel_err(row[:d], f[:d]).max() <= 1e-4
+        assert abs(row[2 * d] - f[2 * d]) <= 1e-4 * max(1.0, f[2 * d])
+        assert abs(row[2 * d + 1] - f[2 * d + 1]) <= 1e-5
+        for c in range(d):
+            if row[d + c] != f[d + c]:
+                vals = pts[:, c]
+                cum_at = np.sum(w[vals <= row[d + c]])
+                assert abs(cum_at - 0.5 * w.sum()) <= 1e-5 * w.sum(), (lin, c)
+
+
+def test_features_list_matches_image_and_rejects_outside_indices(nl):
+    """Rows of a pixel list equal the rows of the whole-image pass bitwise; listed indices outside
+    the image give NaN rows and leave the other rows unchanged."""
+    g, _ = synth.noisy_image(8200, 24, 29, 20.0)
+    gi = torch.from_numpy(g).to(DEV)
+    full = nl.nlem_features(gi, 7, 21, 200.0)
+    pix = torch.tensor([5, 24 * 29, 100, -3, 24 * 29 - 1], dtype=torch.int32, device=DEV)
+    rows = nl.nlem_features(gi, 7, 21, 200.0, pixels=pix)
+    for i, p in enumerate(pix.tolist()):
+        if 0 <= p < 24 * 29:
+            assert torch.equal(rows[i], full[p])
+        else:
+            assert torch.isnan(rows[i]).all()
+
+
 def _fp16_params(ws, seed):
     rng = np.random.default_rng(seed)
     p = (rng.normal(size=ws.num_params) * 0.05).astype(np.float16).astype(np.float32)
