@@ -13,7 +13,9 @@
 //   - weighted mean: a thread per coordinate, summed over the window;
 //   - medians: coordinate c = (pr, pc) of window point j = (jr, jc) is the tile value at
 //     (jr + pr, jc + pc), so every coordinate's values are a shifted copy of one tile.  The tile
-//     is sorted once (bitonic, 64-bit keys: order-preserving value bits, then position).  Per
+//     is sorted once (bitonic, 64-bit keys: order-preserving value bits, then position; each
+//     thread holds 8 consecutive ranks, so distances 1-4 are swapped in registers, 8-128 by warp
+//     shuffles and 256-512 through shared memory: 3 of the 55 stages need a barrier).  Per
 //     coordinate the weights are summed along that order by reading the window's weight map
 //     shifted by c; a zero border gives positions outside the shifted window weight 0.  Weights
 //     are summed exactly, as 64-bit fixed point with 54 fraction bits (w <= 1 and n <= 1024 keep
@@ -54,24 +56,78 @@ __host__ __device__ inline size_t smem_bytes(int S, int K) {
   return 8 * ((size_t)SORT + m * m + (NW + 2) * CHUNK) + 4 * ((size_t)(S + K - 1) * (S + K - 1) + (size_t)S * S);
 }
 
-// Weighted medians of coordinates [C0, C0 + CN): per-thread run sums, a block-wide prefix of
-// them, and a re-walk of the run that crosses half the total.  Starts and ends with a barrier.
-template <int D, int K, int C0, int CN>
-__device__ void medians(const unsigned long long* __restrict__ keys, const unsigned long long* __restrict__ wmap,
-                        unsigned long long* __restrict__ scratch, int NTILE, int TC, int MC, float* __restrict__ fout) {
+// Bitonic sort, ascending, of the SORT keys held RPT per thread in blocked order (thread t holds
+// ranks RPT t .. RPT t + RPT - 1).  On return every thread holds its ranks of the sorted order in
+// kv and the whole sorted order is in buf.
+__device__ __forceinline__ void sort_keys(unsigned long long (&kv)[RPT], unsigned long long* __restrict__ buf) {
+  static_assert(RPT == 8 && SORT == 1024, "the stage split below assumes 8 ranks per thread");
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 2; k <= SORT; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < RPT) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          if ((r & j) == 0) {
+            const bool asc = k < RPT ? (r & k) == 0 : ((t * RPT) & k) == 0;
+            const unsigned long long a = kv[r], b = kv[r | j];
+            const bool sw = (a > b) == asc;
+            kv[r] = sw ? b : a;
+            kv[r | j] = sw ? a : b;
+          }
+        }
+      } else {
+        const bool lower = ((t * RPT) & j) == 0, asc = ((t * RPT) & k) == 0, keep_min = lower == asc;
+        if (j < 32 * RPT) {
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            const unsigned long long o = __shfl_xor_sync(kFull, kv[r], j / RPT);
+            kv[r] = keep_min ? (o < kv[r] ? o : kv[r]) : (o > kv[r] ? o : kv[r]);
+          }
+        } else {
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) buf[t * RPT + r] = kv[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            const unsigned long long o = buf[(t * RPT + r) ^ j];
+            kv[r] = keep_min ? (o < kv[r] ? o : kv[r]) : (o > kv[r] ? o : kv[r]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) buf[t * RPT + r] = kv[r];
+}
+
+// Weighted medians of coordinates [C0, C0 + cn), cn <= CN: per-thread run sums, a block-wide
+// prefix of them, and a re-walk of the run that crosses half the total.  off[r] is the
+// weight-map offset of this thread's rank RPT t + r (-1 for padding).  Starts and ends with a
+// barrier.
+template <int D, int K, int CN>
+__device__ __forceinline__ void medians(const int (&off)[RPT], const unsigned long long* __restrict__ keys,
+                                     const unsigned long long* __restrict__ wmap,
+                                     unsigned long long* __restrict__ scratch, int NTILE, int TC, int MC, int C0,
+                                     int cn, float* __restrict__ fout) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   __syncthreads();
+  // map offset of coordinate C0 + c: coordinate (pr, pc) reads entry (ur - pr + K-1, uc - pc + K-1)
+  int coff[CN];
+#pragma unroll
+  for (int c = 0; c < CN; ++c) coff[c] = c < cn ? ((C0 + c) / K) * MC + (C0 + c) % K : 0;
   unsigned long long acc[CN];
 #pragma unroll
   for (int c = 0; c < CN; ++c) acc[c] = 0ull;
-  for (int r = t * RPT; r < t * RPT + RPT; ++r) {
-    const int u = (int)(unsigned int)keys[r];
-    if (u >= NTILE) break;                                  // padding sorts last
-    const int ur = u / TC, uc = u - ur * TC;
-    // coordinate (pr, pc) reads map entry (ur - pr + K-1, uc - pc + K-1)
-    const unsigned long long* base = wmap + (ur + K - 1) * MC + (uc + K - 1);
 #pragma unroll
-    for (int c = 0; c < CN; ++c) acc[c] += base[-((C0 + c) / K) * MC - ((C0 + c) % K)];
+  for (int r = 0; r < RPT; ++r) {
+    if (off[r] < 0) break;                                  // padding sorts last
+    const unsigned long long* base = wmap + off[r];
+#pragma unroll
+    for (int c = 0; c < CN; ++c) acc[c] += c < cn ? base[-coff[c]] : 0ull;
   }
   unsigned long long incl[CN];
 #pragma unroll
@@ -107,7 +163,7 @@ __device__ void medians(const unsigned long long* __restrict__ keys, const unsig
     }
   }
   __syncthreads();
-  for (int c = t; c < CN; c += NT) {
+  for (int c = t; c < cn; c += NT) {
     const int pr = (C0 + c) / K, pc = (C0 + c) % K, run = xrun[c];
     unsigned long long cum = xlo[c];
     float med = 0.f;
@@ -125,14 +181,14 @@ __device__ void medians(const unsigned long long* __restrict__ keys, const unsig
   __syncthreads();
 }
 
-template <int D, int K, int C0>
-__device__ __forceinline__ void all_medians(const unsigned long long* keys, const unsigned long long* wmap,
-                                            unsigned long long* scratch, int NTILE, int TC, int MC, float* fout) {
-  if constexpr (C0 < D) {
-    constexpr int CN = (D - C0) < CHUNK ? (D - C0) : CHUNK;
-    medians<D, K, C0, CN>(keys, wmap, scratch, NTILE, TC, MC, fout);
-    all_medians<D, K, C0 + CN>(keys, wmap, scratch, NTILE, TC, MC, fout);
-  }
+template <int D, int K>
+__device__ __forceinline__ void all_medians(const int (&off)[RPT], const unsigned long long* keys,
+                                            const unsigned long long* wmap, unsigned long long* scratch, int NTILE,
+                                            int TC, int MC, float* fout) {
+  constexpr int CN = D < CHUNK ? D : CHUNK;
+#pragma unroll
+  for (int c0 = 0; c0 < D; c0 += CN)
+    medians<D, K, CN>(off, keys, wmap, scratch, NTILE, TC, MC, c0, D - c0 < CN ? D - c0 : CN, fout);
 }
 
 // CTA-wide sums of a and b and the maximum of m (deterministic order: warp shuffles, then the
@@ -216,13 +272,7 @@ features_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, f
       swl += w > 0.f ? w * logf(w) : 0.f;
       wmax = fmaxf(wmax, w);
     }
-    // sort keys of the tile: position u = (ur, uc) row-major in the tile
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const int u = t + i * NT;
-      keys[u] = feat_key(u < NTILE ? tile[u] : __int_as_float(0x7f800000), u);   // padding sorts last
-    }
-    block_stats(sw, swl, wmax);   // contains the barrier that publishes wv, wmap and keys
+    block_stats(sw, swl, wmax);   // contains the barrier that publishes wv and wmap
     // weighted mean, a thread per coordinate (the window's rows in order, two partial sums)
     const float inv_w = 1.f / sw;
     for (int q = t; q < D; q += NT) {
@@ -244,22 +294,23 @@ features_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, f
       fout[2 * D] = logf(sw) - swl * inv_w;
       fout[2 * D + 1] = wmax * inv_w;
     }
-    // bitonic sort of the keys, ascending
-    for (int kk = 2; kk <= SORT; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        __syncthreads();
-        for (int pidx = t; pidx < SORT / 2; pidx += NT) {
-          const int i = ((pidx & ~(jj - 1)) << 1) | (pidx & (jj - 1)), partner = i + jj;   // jj: power of 2
-          const bool asc = (i & kk) == 0;
-          const unsigned long long a = keys[i], b = keys[partner];
-          if ((a > b) == asc) {
-            keys[i] = b;
-            keys[partner] = a;
-          }
-        }
-      }
+    // sort keys of the tile (position u = (ur, uc) row-major in the tile), RPT consecutive
+    // positions per thread; padding past the tile sorts last
+    unsigned long long kv[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int u = t * RPT + r;
+      kv[r] = feat_key(u < NTILE ? tile[u] : __int_as_float(0x7f800000), u);
     }
-    all_medians<D, K, 0>(keys, wmap, scratch, NTILE, TC, MC, fout);
+    sort_keys(kv, keys);
+    int off[RPT];   // weight-map offsets of this thread's ranks, decoded once for every chunk
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int u = (int)(unsigned int)kv[r];
+      const int ur = u / TC, uc = u - ur * TC;
+      off[r] = u < NTILE ? (ur + K - 1) * MC + (uc + K - 1) : -1;
+    }
+    all_medians<D, K>(off, keys, wmap, scratch, NTILE, TC, MC, fout);
   }
 }
 
