@@ -104,8 +104,8 @@ PROFILED = {
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.12},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "91ce3712a71ef8dc", "traffic": (361667072 + 4059136) * 64, "fma_pipe_pct": 41.57,
-                        "issue_pct": 35.43, "smem_wavefront_pct": 66.78},
+    "em_batch_kernel": {"sources": "c9c2c2b718e96315", "traffic": (362168064 + 3763712) * 64, "fma_pipe_pct": 41.56,
+                        "issue_pct": 35.43, "smem_wavefront_pct": 66.80},
 }
 
 
