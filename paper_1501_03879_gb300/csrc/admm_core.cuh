@@ -25,9 +25,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "solver_common.cuh"
+
 namespace nlemk {
 
-constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int rup4(int x) { return (x + 3) & ~3; }
 __host__ __device__ constexpr int pow2ceil(int x) { return x <= 1 ? 1 : 2 * pow2ceil((x + 1) / 2); }
@@ -78,15 +79,6 @@ struct Cfg {
   static_assert((CAP + 128) * 2 <= SZ_WRED, "FP64 check scratch must fit the reduction region");
 };
 
-struct SolveParams {
-  float lo, hi;        // box C = [lo, hi]^d
-  float mu, inv_mu;    // penalty (rho) and its inverse
-  int iters;           // iteration cap
-  float tol;           // <= 0: fixed count
-  int check_every;     // residual check period
-  int d;               // runtime dimension (used when D == 0)
-};
-
 template <class C>
 struct Smem {
   float* pts;
@@ -107,13 +99,6 @@ struct Smem {
         cred(reinterpret_cast<float4*>(base + C::OFF_CRED)), scal(base + C::OFF_SCAL),
         tile(base + C::OFF_WRED) {}
 };
-
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
-  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-__device__ __forceinline__ float f4get(const float4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
 
 // Lane mapping: slice g = lane / LPG, point group pg = warp * LPG + lane % LPG, so the G lanes
 // of a point are LPG apart and every 8-lane phase of a 16-byte shared load reads 8
@@ -230,13 +215,6 @@ __device__ __forceinline__ void block_reduce(const Smem<C>& sm, const float (&ac
   block_reduce_rows<C>(sm, tot0, tot1);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-
-__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
 // Weighted sum of the points (sum_j w_j a_j) and sum_j w_j, with w_j = weight of point slot
 // j taken from wreg[p] (0 for inactive slots).  Writes z0 = P_C(sum w a / sum w) into zv and
@@ -305,8 +283,13 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
 // Algorithm 1 from the state set up by the caller: pts (inactive slots zero), lam
 // (lam_j = w_j / mu, zero for inactive slots), zv = cv = z(0) (phantom slots zero) and
 // sgv = 0.  On return zv holds z; scal[2] = iterations run; scal[3] = last residual.
-template <class C>
+// SPLIT (two lanes per point only): thread 0 publishes each iteration's check flag, and the two
+// lanes of a point split the rsqrt of the step s.  The standalone batch kernel measured 3.6%
+// faster with it; the NLEM kernels of one pixel per CTA measured 2-5% slower, so they do not
+// take it (the register allocation decides).
+template <class C, bool SPLIT = false>
 __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm) {
+  static_assert(!SPLIT || C::G == 2, "the split rsqrt pairs the two lanes of a point");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
   const bool last = (g == C::G - 1);
   const float inv_n = 1.f / (float)n;
@@ -329,18 +312,20 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 
   int it = 0;
   float resid = 0.f;
-  // the check schedule (the cap, and every check_every-th iteration with a tolerance): thread 0
-  // keeps a countdown in shared memory and publishes each next iteration's flag, so the other
-  // threads read a flag instead of each computing a remainder
+  // the check schedule (the cap, and every check_every-th iteration with a tolerance).  With
+  // SPLIT, thread 0 keeps a countdown in shared memory and publishes each next iteration's flag,
+  // so the other threads read a flag instead of each computing a remainder.
   int* si = reinterpret_cast<int*>(sm.scal);
-  if (t == 0) {
-    const bool periodic = prm.check_every == 1;
-    si[7] = periodic ? prm.check_every : prm.check_every - 1;
-    si[6] = (1 == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
+  if constexpr (SPLIT) {
+    if (t == 0) {
+      const bool periodic = prm.check_every == 1;
+      si[7] = periodic ? prm.check_every : prm.check_every - 1;
+      si[6] = (1 == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (it = 1; it <= prm.iters; ++it) {
-    const bool check = si[6] != 0;
+    const bool check = SPLIT ? si[6] != 0 : (it == prm.iters) || (prm.tol > 0.f && (it % prm.check_every) == 0);
     // phase 1: e = c + h (in place) and squared norms, one float4 of c at a time; the
     // points are innermost so that consecutive FFMA2s feed different norm accumulators
     float s[C::P];
@@ -378,7 +363,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     // s = min(1, lam / ||e||); r2 = 0 gives lam*inf (or NaN when lam = 0), and fminf then
     // yields 1, which is harmless because e = 0 there.
     float gs = 0.f;
-    if constexpr (C::G == 2) {
+    if constexpr (SPLIT) {
       // the two lanes of a point split the points: a reduce-scatter of the partial norms leaves
       // lane g with the full norm of points 2k+g, which it alone turns into s; the s values are
       // then exchanged (4 rsqrt per lane instead of 7)
@@ -505,7 +490,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     block_reduce_rows<C>(sm, t0, t1);
     // finalize (warp 0): z+ = P_C(z - sum g / n), c+ = 2 z+ - z, residuals on checks
     if (t < 32) {
-      if (t == 0) {   // the next iteration's check flag (read by every thread after the barrier)
+      if (SPLIT && t == 0) {   // the next iteration's check flag (read by every thread after the barrier)
         const int cnt = si[7];
         const bool periodic = cnt == 1;
         si[7] = periodic ? prm.check_every : cnt - 1;

@@ -135,6 +135,7 @@ int nlem_ctx_destroy(nlem_ctx* ctx) {
   cudaFree(ctx->ws_x0);
   cudaFree(ctx->ws_rho);
   cudaFree(ctx->ws_list);
+  cudaFree(ctx->ws_ulist);
   cudaFree(ctx->ws_count);
   cudaFree(ctx->ws_em);
   for (int i = 0; i < 2; ++i) {

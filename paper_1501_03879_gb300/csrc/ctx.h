@@ -55,6 +55,8 @@ struct nlem_ctx {
   float* ws_x0 = nullptr;
   float* ws_rho = nullptr;
   int* ws_list = nullptr;
+  int* ws_ulist = nullptr;         // a caller's pixel list with the entries outside the image removed
+  size_t ws_ulist_cap = 0;
   long long* ws_count = nullptr;   // device element counts: [0] fallback list, [1] caller list
   size_t ws_warm_pixels = 0;
   int ws_warm_d = 0;

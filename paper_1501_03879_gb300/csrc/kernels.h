@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "admm_core.cuh"
+#include "solver_common.cuh"
 
 namespace nlemk {
 

@@ -7,7 +7,7 @@
 // shared-memory traffic of one problem per CTA), and one set of CTA barriers per iteration
 // serves both problems (twice the work between synchronisations).
 //
-// Per-point algebra (Algorithm 1 in the reformulation of admm_core.cuh, FP32):
+// Per-point algebra (Algorithm 1 in the reformulation used by the one-problem solver, FP32):
 //   e = c + h,  s = min(1, lam / ||e||),  sum_g += s e,  h = s e - a,
 // with c = 2 z(t) - z(t-1) per problem and h_k = g_k - a_k started at -a_k.
 //
@@ -35,8 +35,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include "admm_core.cuh"
 #include "kernels.h"
+#include "solver_common.cuh"
 
 namespace nlemk {
 namespace pairk {

@@ -82,7 +82,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       }
       weighted_mean_start<C>(sm, wreg, n, dd, prm);
     }
-    admm_iterate<C>(sm, n, dd, prm);
+    admm_iterate<C, C::G == 2>(sm, n, dd, prm);
     for (int q = t; q < dd; q += C::NT) {
       const int sg = q / C::Q, i = q - sg * C::Q;
       x_out[(size_t)b * dd + q] = sm.zv[sg * C::QA + i];
@@ -279,7 +279,6 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
   const long long items = pix_list ? *n_list : (long long)H * W;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const long long pix = pix_list ? (long long)pix_list[it] : it;
-    if (pix < 0 || pix >= (long long)H * W) continue;   // a listed index outside the image is skipped
     nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
                      wtab, ex);
   }

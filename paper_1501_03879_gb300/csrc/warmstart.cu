@@ -257,6 +257,24 @@ __global__ void fallback_list_kernel(const int* __restrict__ iters_used, long lo
   }
 }
 
+// the entries of a caller's pixel list that lie in [0, total), in any order, and their count
+// (one atomic per warp: the ballot of valid entries and their ranks within the warp)
+__global__ void compact_list_kernel(const int* __restrict__ in, long long n, long long total, int* __restrict__ out,
+                                    long long* __restrict__ count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    const int v = i < n ? in[i] : -1;
+    const bool ok = i < n && v >= 0 && (long long)v < total;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    unsigned long long pos = 0;
+    if (lane == 0 && m) pos = atomicAdd(reinterpret_cast<unsigned long long*>(count), (unsigned long long)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (ok) out[pos + __popc(m & ((1u << lane) - 1u))] = v;
+  }
+}
+
 __global__ void gather_rows_kernel(const float* __restrict__ src, int cols, const int* __restrict__ rows,
                                    long long nrows, float* __restrict__ dst) {
   const long long total = nrows * cols;
@@ -335,6 +353,13 @@ int ws_apply(const float* feats, const float* y, long long B, int d, float lo, f
 int ws_gather_rows(const float* src, int cols, const int* rows, long long nrows, float* dst, int sm_count,
                    cudaStream_t s) {
   gather_rows_kernel<<<grid_for(nrows * cols, 256, sm_count), 256, 0, s>>>(src, cols, rows, nrows, dst);
+  return (int)cudaGetLastError();
+}
+
+int ws_compact_list(const int* in, long long n, long long total, int* out, long long* count, int sm_count,
+                    cudaStream_t s) {
+  cudaMemsetAsync(count, 0, sizeof(long long), s);
+  if (n > 0) compact_list_kernel<<<grid_for(n, 256, sm_count), 256, 0, s>>>(in, n, total, out, count);
   return (int)cudaGetLastError();
 }
 

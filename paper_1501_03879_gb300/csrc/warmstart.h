@@ -39,6 +39,10 @@ int ws_apply(const float* feats, const float* y, long long B, int d, float lo, f
 // dst[r][c] = src[rows[r]][c] for r < nrows, c < cols (minibatch gather).
 int ws_gather_rows(const float* src, int cols, const int* rows, long long nrows, float* dst, int sm_count,
                    cudaStream_t s);
+// The entries of in[0, n) that lie in [0, total), compacted into out (any order), their count in
+// *count (device).
+int ws_compact_list(const int* in, long long n, long long total, int* out, long long* count, int sm_count,
+                    cudaStream_t s);
 int ws_fallback_list(const int* iters_used, long long npix, int cap, int* list, long long* count, int sm_count,
                      cudaStream_t s);
 

@@ -427,9 +427,13 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
   if ((rc = ensure_counts(ctx))) return rc;
   if (pixels) {
     if (npix == 0) return NLEM_OK;
-    long long n = npix;
-    cudaMemcpyAsync(ctx->ws_count + 1, &n, sizeof(long long), cudaMemcpyHostToDevice, s);
-    L.pix_list = pixels;
+    // the solver reads a copy of the list without the entries outside the image (their count on
+    // the device), so its item loop needs no bounds test
+    if ((rc = grow(&ctx->ws_ulist, &ctx->ws_ulist_cap, (size_t)npix, "pixel list"))) return rc;
+    const int ce = nlemk::ws_compact_list(pixels, npix, (long long)H * W, ctx->ws_ulist, ctx->ws_count + 1,
+                                          ctx->sm_count, s);
+    if (ce) return wfail(NLEM_ERR_CUDA, "pixel list: %s", cudaGetErrorString((cudaError_t)ce));
+    L.pix_list = ctx->ws_ulist;
     L.n_list = ctx->ws_count + 1;
     L.max_items = npix;
   }

@@ -169,6 +169,29 @@ def test_per_pixel_start_and_penalty(nl):
         assert rel_err(out[lin], zo[24]) <= TOL
 
 
+def test_pixel_list_entries_outside_the_image_are_skipped(nl):
+    """A pixel list with entries outside [0, H*W) (negative, past the end) and a duplicate: the valid
+    pixels get the same values as the whole-image solve, the other outputs keep what they held."""
+    g, _ = synth.noisy_image(8150, 20, 23, 20.0)
+    H, W = g.shape
+    img = torch.from_numpy(g).to(DEV)
+    full = nl.nlem_denoise(img, patch=7, window=11, h=200.0, rho=1.0, iters=30, layout=nl.LAYOUT_PIXEL)
+    pix = torch.tensor([-1, 7, H * W, 200, 7, 2 ** 30, H * W - 1], dtype=torch.int32, device=DEV)
+    sentinel = -12345.0
+    o = dict(out=torch.full((H, W), sentinel, device=DEV), iters_used=torch.full((H, W), -7, dtype=torch.int32, device=DEV),
+             residual=torch.zeros((H, W), device=DEV))
+    nl.nlem_denoise_ex(img, 7, 11, 200.0, rho=1.0, iters=30, pixels=pix, out=o)
+    got = o["out"].reshape(-1).cpu()
+    ref = full["out"].reshape(-1).cpu()
+    valid = [7, 200, H * W - 1]
+    for p in valid:
+        assert got[p] == ref[p]
+    mask = torch.ones(H * W, dtype=torch.bool)
+    mask[valid] = False
+    assert torch.all(got[mask] == sentinel)
+    assert torch.all(o["iters_used"].reshape(-1).cpu()[mask] == -7)
+
+
 def test_trained_warm_start_gains_over_plain_admm(nl):
     """Train on solves of two synthetic images, evaluate on a held-out one: the learned start and
     penalty reach the 1e-4 residual in far fewer iterations than plain EM-ADMM (rho = 1) and
