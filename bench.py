@@ -101,7 +101,7 @@ KERNEL_SOURCES = {
                         _CSRC + "shapes.h"],
 }
 PROFILED = {
-    "nlem_pair_kernel": {"sources": "429400d1bb3111d2", "traffic": (132352 + 0) * 16, "fma_pipe_pct": 47.81,
+    "nlem_pair_kernel": {"sources": "c60374d08efe0777", "traffic": (133632 + 0) * 16, "fma_pipe_pct": 47.81,
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.12},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
