@@ -87,8 +87,8 @@ NLEM_KERNEL = "nlem_pair_kernel"
 EM_KERNEL = "em_batch_kernel"
 
 # Counters of the ncu captures summarised in profiles/, each valid only for the sources its kernel
-# was built from (hash of the files below); a kernel whose sources changed since reports null
-# until a new capture is recorded.  traffic = dram__bytes_read.sum + dram__bytes_write.sum per
+# was built from (hash of the code of the files below, comments and whitespace ignored); a kernel
+# whose code changed since reports null until a new capture is recorded.  traffic = dram__bytes_read.sum + dram__bytes_write.sum per
 # full launch, scaled from the small case by units processed; the percentages are
 # sm__pipe_fma_cycles_active, smsp__issue_active and the shared-memory wavefronts, each as a
 # fraction of peak over the captured launch.
@@ -101,21 +101,30 @@ KERNEL_SOURCES = {
                         _CSRC + "shapes.h"],
 }
 PROFILED = {
-    "nlem_pair_kernel": {"sources": "c60374d08efe0777", "traffic": (133632 + 0) * 16, "fma_pipe_pct": 47.81,
+    "nlem_pair_kernel": {"sources": "9421c35fcc4ed44a", "traffic": (133632 + 0) * 16, "fma_pipe_pct": 47.81,
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.12},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "77bed10347a188fb", "traffic": (361474560 + 3775744) * 64, "fma_pipe_pct": 41.57,
+    "em_batch_kernel": {"sources": "f493a2c1c688dffa", "traffic": (361474560 + 3775744) * 64, "fma_pipe_pct": 41.57,
                         "issue_pct": 35.43, "smem_wavefront_pct": 66.81},
 }
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed: what the compiler sees."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_hash(kernel):
+    """Hash of the code (comments and whitespace ignored) of the files a kernel is built from."""
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -28,6 +28,12 @@
 //   c = 3     (A tail sum, A ||dh||^2, A ||g||^2)  c = 7     (B tail sum, B ||dh||^2, B ||g||^2)
 // z, c = 2z - z_prev, sum g and the centre patches are kept in the same column layout, each
 // slice padded to 9 float4 so that the broadcast loads of the 4 slices hit different banks.
+// Warp 0 forms z+ and c+ branch-free and publishes the next iteration's check flag.
+//
+// The step s of the 14 (point, problem) pairs of a point group: the partial norms are
+// reduce-scattered over the group's 4 lanes, each lane turns its own full norms into s (4 rsqrt
+// instead of 14), and the s values are gathered back.  The tail coordinate is updated as a
+// fourth point quad in the prefetched update loop.
 //
 // Each problem stops at its own residual check (or the cap): its z is frozen from then on and
 // the CTA runs until both are frozen, so the result of each pixel is the iterate at which its
