@@ -51,3 +51,10 @@ def test_counters_reported_only_for_unchanged_sources(monkeypatch):
     stale[kernel] = dict(good[kernel], sources="0" * 16)
     monkeypatch.setattr(b, "PROFILED", stale)
     assert kernel not in b.profiled_counters()
+
+
+def test_source_hash_ignores_comments_and_whitespace():
+    b = _bench()
+    assert b._code_only("int a; // note\n  /* block\n comment */ float b;\n\n") == "int a; float b;"
+    assert b._code_only("x = 1; // one") == b._code_only("x =\t1;\n")
+    assert b._code_only("x = 1;") != b._code_only("x = 2;")
