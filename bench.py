@@ -12,8 +12,9 @@ One step = one pass over the production workload:
 Every pixel and every standalone problem is one EM solve; `value` is EM solves per second
 over the whole step (inputs resident in HBM), `mpixel_per_s` the NLEM part alone.  `e2e` is the
 same step through the public API with host buffers (nlem_denoise_host, em_solve_batch_host), the
-copies inside the timed region; the batch entry point overlaps each chunk's upload with the
-previous chunk's solve.
+copies inside the timed region.  The batch runs on a second host thread with its own context and
+stream, so its upload and solve overlap the NLEM images; within the batch, each chunk's upload
+overlaps the previous chunk's solve.
 
 At one GPU the line also carries `extras`, each timed on its own after the main measurement:
 rho = 1e-3 on the same images; the paper's setting (mu = 1e-3, 4 iterations, noisy-patch
@@ -612,22 +613,36 @@ def main():
         torch.cuda.synchronize()
 
         parts = {"nlem_host_ms": 0.0, "em_host_ms": 0.0}
+        # the batch runs on a second host thread with its own context and stream (one context per
+        # host thread), so its 22.6 GB upload and its solve overlap the NLEM images on the first
+        ctx_em = nl.Context(local)
+        em_stream = torch.cuda.Stream(device=dev)
+
+        def em_part(box_out):
+            t0 = time.perf_counter()
+            with torch.cuda.stream(em_stream):
+                nl.em_solve_batch_host(host_pts, host_w, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK,
+                                       ctx=ctx_em, out=host_em, device=local)
+            box_out.append(time.perf_counter() - t0)
 
         def e2e_step(record=False):
             # the host-buffer entry points copy in and out inside the library (each call returns
             # with its results on the host); the batch solve overlaps each chunk's upload with the
             # previous chunk's solve
+            em_t = []
+            th = threading.Thread(target=em_part, args=(em_t,))
             ta = time.perf_counter()
+            th.start()
             for i, sg in enumerate(SIGMAS):
                 nl.nlem_denoise_host(host_imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=RHO, iters=CAP,
                                      box=BOX, tol=TOL, check_every=CHECK, ctx=ctx, out=host_out[i], device=local)
             tb = time.perf_counter()
-            nl.em_solve_batch_host(host_pts, host_w, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK,
-                                   ctx=ctx, out=host_em, device=local)
-            tc = time.perf_counter()
+            th.join()
+            if not em_t:
+                raise RuntimeError("the batch part of the end-to-end step failed")
             if record:
                 parts["nlem_host_ms"] += 1e3 * (tb - ta)
-                parts["em_host_ms"] += 1e3 * (tc - tb)
+                parts["em_host_ms"] += 1e3 * em_t[0]
 
         e2e_step()
         if world > 1:
