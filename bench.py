@@ -17,8 +17,10 @@ stream, so its upload and solve overlap the NLEM images; within the batch, each 
 overlaps the previous chunk's solve.
 
 At one GPU the line also carries `extras`, each timed on its own after the main measurement:
-rho = 1e-3 on the same images; the paper's setting (mu = 1e-3, 4 iterations, noisy-patch
-start) with PSNR; BF16 tensor-core weights against FP32 on a 1024x1024 image with impulse
+rho = 1e-3 on the same images; the Table 1 protocol of Sec. 3 (NLM, NLEM-IRLS and NLEM-ADMM
+PSNR over 10 noise realisations at sigma 10..80, 4 iterations); synthetic analogues of Figs. 1
+and 2 (PSNR and objective against iteration, ADMM vs IRLS); BF16 tensor-core weights against
+FP32 on a 1024x1024 image with impulse
 noise; 64 uneven images in one persistent graph-captured launch; and the learned warm start on
 a 2048x2048 image against plain EM-ADMM.  --no-extras skips them.
 
@@ -65,7 +67,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--profile-case", choices=["traffic", "bf16", "features"], default=None,
+    p.add_argument("--profile-case", choices=["traffic", "bf16", "features", "irls"], default=None,
                    help="run a small profiling case (no timing output) and exit")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra rows (rho=1e-3, mixed precision, batch, learned warm start)")
@@ -140,7 +142,8 @@ def profile_case(which="traffic"):
     traffic: NLEM on a 128x128 image and 4096 standalone problems with the benchmark's
     per-problem settings.  bf16: the tensor-core weight table of a 256x256 image (sigma 30 + 5%
     impulses, 9x9 patches, 21x21 window).  features: the warm-start features of a 256x256 image
-    (7x7 patches, 21x21 window)."""
+    (7x7 patches, 21x21 window).  irls: NLEM-IRLS, 40 steps from the noisy patch, on a 128x128
+    image (sigma 20, h = 200, 7x7 patches, 21x21 window)."""
     import torch
     import synth
     import paper_1501_03879_gb300 as nl
@@ -153,6 +156,14 @@ def profile_case(which="traffic"):
                 nl.nlem_bf16_weights(gi, 9, 21, 300.0)
             else:
                 nl.nlem_features(gi, 7, 21, 250.0)
+        torch.cuda.synchronize()
+        return
+    if which == "irls":
+        g, _ = synth.noisy_image(10012, 128, 128, 20.0)
+        gi = torch.from_numpy(g).to(dev)
+        for _ in range(2):
+            nl.nlem_denoise(gi, patch=K_PATCH, window=S_WIN, h=200.0, iters=40, init=nl.INIT_NOISY_PATCH,
+                            solver=nl.SOLVER_IRLS)
         torch.cuda.synchronize()
         return
     g, _ = synth.noisy_image(10011, 128, 128, 20.0)
@@ -175,6 +186,7 @@ def profile_case(which="traffic"):
 #   per (problem, iteration): 8*n*d + 4*n FP32 flops
 #   per NLEM pixel once: 3*n*d (distances) + 2*n*d (weighted mean) + 3*n (exp)
 #   per standalone problem once: 2*n*d (weighted mean)
+#   per (problem, IRLS step): 5*n*d + 4*n (x - a, ||.||^2, sum om a; rsqrt, weight, sum om)
 # ------------------------------------------------------------------------------------------
 def window_counts(Hh, Ww, S):
     R = (S - 1) // 2
@@ -187,6 +199,10 @@ def window_counts(Hh, Ww, S):
 
 def nlem_flops(n_map, iters_map, d):
     return float(np.sum((8.0 * n_map * d + 4.0 * n_map) * iters_map + 5.0 * n_map * d + 3.0 * n_map))
+
+
+def irls_flops(n_map, steps, d):
+    return float(np.sum((5.0 * n_map * d + 4.0 * n_map) * steps + 5.0 * n_map * d + 3.0 * n_map))
 
 
 def em_flops(iters, n, d):
@@ -433,25 +449,105 @@ def extra_warm_start(nl, ctx, n_train):
             "speedup_vs_plain_rho1": ms_p / ms_w, "speedup_vs_best_rho": ms_b / ms_w}
 
 
-def extra_paper_setting(nl, ctx):
-    """The paper's own denoising setting (Sec. 3): 7x7 patches, 21x21 window, h = 10 sigma,
-    mu = 1e-3, 4 iterations from the noisy patch, on the production-size synthetic images:
-    throughput, and PSNR of the noisy input, of NLM (the weighted-mean start) and of NLEM."""
+TABLE1_SIGMAS = (10.0, 20.0, 40.0, 60.0, 80.0)
+TABLE1_REALISATIONS = 10
+IRLS_EPS = 1e-6
+
+
+def _noisy_realisation(f, sigma, seed):
+    """The clean image f plus sigma times a seeded N(0,1) field (Sec. 3 noise model, not clipped)."""
+    import synth
+    return np.ascontiguousarray((f + sigma * synth.gaussian(seed, f.size).reshape(f.shape)).astype(np.float32))
+
+
+def extra_table1(nl, ctx):
+    """Table 1 protocol of Sec. 3 on a production-size synthetic image: 7x7 patches, 21x21 window,
+    h = 10 sigma, sigma in {10, 20, 40, 60, 80}, PSNR averaged over 10 noise realisations, for NLM (the
+    weighted-mean patch), NLEM-IRLS (eps = 1e-6) and NLEM-ADMM (mu = 1e-3), both 4 iterations from
+    the noisy patch for sigma <= 60 and from the NLM patch above.  Throughput of each solver is
+    timed on the first realisation."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
+    f = synth.clean_image(SEED * 10 + 800, H, W)
     rows = []
-    for i, sg in enumerate(SIGMAS):
-        g, f = synth.noisy_image(SEED * 10 + 700 + i, H, W, sg)
-        img = torch.from_numpy(g).to(dev)
-        ms, r = _timed(lambda: nl.nlem_denoise(img, patch=K_PATCH, window=S_WIN, h=10 * sg, rho=1e-3, iters=4, box=BOX,
-                                               init=nl.INIT_NOISY_PATCH, ctx=ctx), reps=3)
-        nlm = nl.nlem_denoise(img, patch=K_PATCH, window=S_WIN, h=10 * sg, rho=1.0, iters=0, box=BOX, ctx=ctx)
-        rows.append({"sigma": sg, "mpixel_per_s": H * W / (ms * 1e-3) / 1e6,
-                     "psnr_noisy": synth.psnr(g, f), "psnr_nlm": synth.psnr(nlm["out"].cpu().numpy(), f),
-                     "psnr_nlem": synth.psnr(r["out"].cpu().numpy(), f)})
-    return {"workload": "512x512 synthetic, 7x7 patches, 21x21 window, h=10 sigma, mu=1e-3, 4 iterations, "
-                        "noisy-patch start", "rows": rows}
+    for si, sg in enumerate(TABLE1_SIGMAS):
+        init = nl.INIT_NOISY_PATCH if sg <= 60 else nl.INIT_WEIGHTED_MEAN
+        kw = dict(patch=K_PATCH, window=S_WIN, h=10 * sg, box=BOX, init=init, ctx=ctx)
+        ps = {"noisy": [], "nlm": [], "irls": [], "admm": []}
+        ms_irls = ms_admm = None
+        for r in range(TABLE1_REALISATIONS):
+            g = _noisy_realisation(f, sg, SEED * 1000 + 100 * si + r)
+            img = torch.from_numpy(g).to(dev)
+            nlm = nl.nlem_denoise(img, rho=1.0, iters=0, **kw)["out"].cpu().numpy()
+            if r == 0:
+                ms_irls, ri = _timed(lambda: nl.nlem_denoise(img, iters=4, solver=nl.SOLVER_IRLS, irls_eps=IRLS_EPS,
+                                                             **kw), reps=3)
+                ms_admm, ra = _timed(lambda: nl.nlem_denoise(img, rho=1e-3, iters=4, **kw), reps=3)
+            else:
+                ri = nl.nlem_denoise(img, iters=4, solver=nl.SOLVER_IRLS, irls_eps=IRLS_EPS, **kw)
+                ra = nl.nlem_denoise(img, rho=1e-3, iters=4, **kw)
+            ps["noisy"].append(synth.psnr(g, f))
+            ps["nlm"].append(synth.psnr(nlm, f))
+            ps["irls"].append(synth.psnr(ri["out"].cpu().numpy(), f))
+            ps["admm"].append(synth.psnr(ra["out"].cpu().numpy(), f))
+        row = {"sigma": sg, "init": "noisy patch" if init == nl.INIT_NOISY_PATCH else "NLM"}
+        row.update({"psnr_" + k: float(np.mean(v)) for k, v in ps.items()})
+        row["psnr_admm_std"] = float(np.std(ps["admm"]))
+        nmap = window_counts(H, W, S_WIN)
+        d = K_PATCH * K_PATCH
+        row["irls_mpixel_per_s"] = H * W / (ms_irls * 1e-3) / 1e6
+        row["admm_mpixel_per_s"] = H * W / (ms_admm * 1e-3) / 1e6
+        row["irls_tflops"] = irls_flops(nmap, 4, d) / (ms_irls * 1e-3) / 1e12
+        row["admm_tflops"] = nlem_flops(nmap, np.full_like(nmap, 4.0), d) / (ms_admm * 1e-3) / 1e12
+        rows.append(row)
+    return {"workload": f"{H}x{W} synthetic, 7x7 patches, 21x21 window, h=10 sigma, {TABLE1_REALISATIONS} noise "
+                        "realisations per sigma, 4 iterations (ADMM mu=1e-3, IRLS eps=1e-6)", "rows": rows}
+
+
+def extra_convergence(nl, ctx):
+    """Synthetic analogues of Figs. 1 and 2 of Sec. 3.
+    psnr_vs_iter: PSNR after t = 1..10 iterations of NLEM-ADMM (mu = 1e-3) and NLEM-IRLS
+    (eps = 1e-6) from the noisy patch, on the 512x512 synthetic image at sigma 10 and 40.
+    objective_vs_iter: on a 256x256 image at sigma 40, the objective of problem (1) at every pixel
+    (FP64, on the GPU) after t = 1..8 iterations of each solver, against the best value any run
+    reached (500 ADMM iterations included): the median relative gap over the pixels, and the
+    share of pixels within 1e-3 of it (the objective to three significant decimals)."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = synth.clean_image(SEED * 10 + 900, H, W)
+    psnr_rows = []
+    for sg in (10.0, 40.0):
+        img = torch.from_numpy(_noisy_realisation(f, sg, SEED * 1000 + 900 + int(sg))).to(dev)
+        kw = dict(patch=K_PATCH, window=S_WIN, h=10 * sg, box=BOX, init=nl.INIT_NOISY_PATCH, ctx=ctx)
+        for t in range(1, 11):
+            a = nl.nlem_denoise(img, rho=1e-3, iters=t, **kw)["out"].cpu().numpy()
+            b = nl.nlem_denoise(img, iters=t, solver=nl.SOLVER_IRLS, irls_eps=IRLS_EPS, **kw)["out"].cpu().numpy()
+            psnr_rows.append({"sigma": sg, "iters": t, "psnr_admm": synth.psnr(a, f), "psnr_irls": synth.psnr(b, f)})
+    Hs = Ws = 256
+    fs = synth.clean_image(SEED * 10 + 901, Hs, Ws)
+    img = torch.from_numpy(_noisy_realisation(fs, 40.0, SEED * 1000 + 990)).to(dev)
+    kw = dict(patch=K_PATCH, window=S_WIN, h=400.0, box=BOX, init=nl.INIT_NOISY_PATCH, ctx=ctx, fp64_check=True)
+    runs = {}
+    for t in range(1, 9):
+        runs[("admm", t)] = nl.nlem_denoise(img, rho=1e-3, iters=t, **kw)["obj64"].cpu().numpy()
+        runs[("irls", t)] = nl.nlem_denoise(img, iters=t, solver=nl.SOLVER_IRLS, irls_eps=IRLS_EPS,
+                                            **kw)["obj64"].cpu().numpy()
+    best = nl.nlem_denoise(img, rho=1e-3, iters=500, **kw)["obj64"].cpu().numpy()
+    for v in runs.values():
+        best = np.minimum(best, v)
+    obj_rows = []
+    for t in range(1, 9):
+        row = {"iters": t}
+        for m in ("admm", "irls"):
+            gap = (runs[(m, t)] - best) / best
+            row[f"median_gap_{m}"] = float(np.median(gap))
+            row[f"within_1e-3_{m}"] = float(np.mean(gap <= 1e-3))
+        obj_rows.append(row)
+    return {"psnr_vs_iter": psnr_rows,
+            "objective_vs_iter": {"workload": f"{Hs}x{Ws} synthetic, sigma 40, h=400, 7x7 patches, 21x21 window, "
+                                              "noisy-patch start", "rows": obj_rows}}
 
 
 def run_extras(nl, ctx, imgs, args):
@@ -464,7 +560,8 @@ def run_extras(nl, ctx, imgs, args):
         pass
     out = {}
     out["rho_1e-3"] = extra_small_rho(nl, ctx, imgs)
-    out["paper_setting"] = extra_paper_setting(nl, ctx)
+    out["table1"] = extra_table1(nl, ctx)
+    out["convergence"] = extra_convergence(nl, ctx)
     out["bf16"] = extra_mixed_precision(nl, ctx, peaks)
     out["batch"] = extra_batch(nl, ctx)
     out["warm_start"] = extra_warm_start(nl, ctx, args.ws_train)

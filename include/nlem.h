@@ -37,6 +37,10 @@ extern "C" {
 #define NLEM_INIT_WEIGHTED_MEAN 0   /* z0 = P_C(sum w_j P_j / sum w_j): the NLM patch (Sec. 3) */
 #define NLEM_INIT_NOISY_PATCH 1     /* z0 = P_C(P_i): the noisy patch (Sec. 3) */
 
+#define NLEM_SOLVER_ADMM 0          /* EM-ADMM, Algorithm 1 (Sec. 2) */
+#define NLEM_SOLVER_IRLS 1          /* IRLS on the smooth surrogate of Eq. 2 (Sec. 1), the comparison
+                                       method of Sec. 3 (nlem_denoise only) */
+
 #define NLEM_LAYOUT_AUTO 0          /* nlem_denoise picks the problem-to-CTA layout */
 #define NLEM_LAYOUT_PIXEL 1         /* one pixel's problem per CTA */
 #define NLEM_LAYOUT_PAIR 2          /* two horizontally adjacent pixels per CTA, sharing the points
@@ -59,8 +63,10 @@ typedef struct {
   int fp64_check;     /* != 0: also compute, in FP64 on the GPU, the objective of problem (1)
                          and its optimality residual at the returned point (see outputs) */
   int layout;         /* NLEM_LAYOUT_* (nlem_denoise only); PAIR where the pair kernel does not
-                         apply (BF16 precision, other patch sizes, window > 21) is -5 */
-  int reserved[2];
+                         apply (BF16 precision, other patch sizes, window > 21, IRLS) is -5 */
+  int solver;         /* NLEM_SOLVER_* (default ADMM).  IRLS is taken by nlem_denoise and
+                         nlem_denoise_host only; every other entry point returns -1 for it */
+  float irls_eps;     /* epsilon of the surrogate (Eq. 2), >= 1e-30 (default 1e-6) */
 } nlem_options;
 
 void nlem_options_default(nlem_options* opt);
@@ -152,6 +158,13 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
  * pixel per CTA; AUTO takes PAIR for patch 7 in FP32 with window 17..21 and PIXEL otherwise.
  * Each pixel still stops at its own residual check, so the layouts differ only by FP32
  * rounding order.
+ * opt->solver = NLEM_SOLVER_IRLS (NLEM-IRLS, the comparison method of Sec. 3): each pixel's
+ * problem is solved by IRLS on the surrogate of Eq. 2 instead of EM-ADMM,
+ *     x <- P_C(sum_k om_k a_k / sum_k om_k),  om_k = w_k (||x - a_k||^2 + irls_eps)^(-1/2),
+ * from the same start point, for exactly `iters` steps (opt->tol must be <= 0; rho is not
+ * used but must still be valid).  iters_used = iters; residual = ||x(T) - x(T-1)|| / ||x(T)||
+ * of the last step; obj64 / kkt64 as for EM-ADMM (the objective of problem (1) at x(T)).
+ * One pixel per CTA (layout PAIR is -5); patch 5, 7 or 9.
  * Errors: -1 if patch or window is even or < 1, patch > min(H, W),
  * h <= 0, rho <= 0, iters < 0, lo > hi; -5 if patch*patch > 128 or the window holds more
  * points than the kernels support (window <= 31).

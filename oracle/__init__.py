@@ -32,6 +32,8 @@ PINS = {
     "residuals": "r_pri / r_dual against their definitions on stored iterates (step-by-step replay)",
     "nlem": "patch/weight assembly against numpy.pad reflect; constant image; S=1; k=1 weighted median",
     "irls": "surrogate stationarity; converges to the EM within sqrt(eps)-scale",
+    "nlem_irls": "k=1 windows: the weighted median of the window's pixels after many steps; constant "
+                 "image; one pixel equals irls on nlem_problem; zero steps give the start point",
     "weiszfeld": "objective non-increasing; agrees with ADMM at convergence",
     "features": "weighted median: dominant weight, equal weights (ordinary median), d=1 problem (1) "
                 "solution; entropy of uniform weights = log n; weighted mean = 1-point mean",
@@ -257,6 +259,35 @@ def nlem_problem(img, k, S, h, lin, weight_mode=0):
     n = _load().orc_nlem_problem(_fp(img), H, W, int(k), int(S), float(h), int(lin), int(weight_mode),
                                  _dp(pts), _dp(w), _dp(pc))
     return pts[:n].copy(), w[:n].copy(), pc
+
+
+def nlem_irls(img, k, S, h, eps, iters, lo=0.0, hi=255.0, init_mode=0, pixels=None):
+    """NLEM-IRLS, the comparison method of Sec. 3 (Table 1, Figs. 1-2): every listed pixel's
+    problem (nlem_problem: patches, window, weights exp(-||P_i - P_j||^2 / h^2)) solved by IRLS on
+    the surrogate of Eq. 2 (irls, projected onto [lo, hi]^d after every step) for exactly `iters`
+    steps, from P_C(weighted mean) (init_mode 0) or the projected noisy patch (init_mode 1).
+    Pure composition of nlem_problem, weighted_mean_start, project_box, irls and objective.
+    Returns dict(out, step, obj) of float64 arrays: the centre coordinate of x(T),
+    ||x(T) - x(T-1)|| / ||x(T)|| (0 when iters == 0) and the objective of problem (1) at x(T)."""
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    H, W = img.shape
+    lins = np.arange(H * W) if pixels is None else np.asarray(pixels, dtype=np.int64).reshape(-1)
+    out = np.empty(lins.size)
+    step = np.zeros(lins.size)
+    obj = np.empty(lins.size)
+    c = (k * k - 1) // 2
+    for i, lin in enumerate(lins):
+        pts, w, pc = nlem_problem(img, k, S, h, int(lin))
+        x = weighted_mean_start(pts, w, lo, hi) if init_mode == 0 else project_box(pc, lo, hi)
+        if iters > 0:
+            xp, _ = irls(pts, w, lo, hi, x, eps, iters - 1) if iters > 1 else (x, None)
+            x, _ = irls(pts, w, lo, hi, xp, eps, 1)
+            step[i] = np.linalg.norm(x - xp) / max(np.linalg.norm(x), 1e-300)
+        out[i] = x[c]
+        obj[i] = objective(x, pts, w)
+    if pixels is None:
+        out, step, obj = out.reshape(H, W), step.reshape(H, W), obj.reshape(H, W)
+    return dict(out=out, step=step, obj=obj)
 
 
 def features(pts, w):

@@ -19,6 +19,8 @@ from ._binding import (  # noqa: F401
     LAYOUT_PIXEL,
     PREC_BF16,
     PREC_FP32,
+    SOLVER_ADMM,
+    SOLVER_IRLS,
     Context,
     WarmStart,
     NlemError,

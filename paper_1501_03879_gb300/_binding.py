@@ -12,6 +12,8 @@ PREC_FP32 = 0
 PREC_BF16 = 1
 INIT_WEIGHTED_MEAN = 0
 INIT_NOISY_PATCH = 1
+SOLVER_ADMM = 0
+SOLVER_IRLS = 1
 LAYOUT_AUTO = 0
 LAYOUT_PIXEL = 1
 LAYOUT_PAIR = 2
@@ -39,7 +41,7 @@ class _ImageDesc(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("layout", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("solver", ctypes.c_int), ("irls_eps", ctypes.c_float)]
 
 
 _lib = None
@@ -159,7 +161,7 @@ def _stream(device):
 
 
 def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False,
-             layout=0):
+             layout=0, solver=None, irls_eps=None):
     o = _Options()
     load_library().nlem_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -168,6 +170,10 @@ def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEA
     o.init = int(init)
     o.fp64_check = 1 if fp64_check else 0
     o.layout = int(layout)
+    if solver is not None:
+        o.solver = int(solver)
+    if irls_eps is not None:
+        o.irls_eps = float(irls_eps)
     return o
 
 
@@ -303,10 +309,11 @@ def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x
 
 def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                  precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None,
-                 out=None, layout=LAYOUT_AUTO):
+                 out=None, layout=LAYOUT_AUTO, solver=SOLVER_ADMM, irls_eps=1e-6):
     """NLEM (Sec. 3) of a float32 CUDA image [H, W].  Returns dict(out [H,W], iters_used,
     residual[, obj64, kkt64]).  layout: LAYOUT_AUTO, LAYOUT_PIXEL (one pixel per CTA) or
-    LAYOUT_PAIR (two adjacent pixels per CTA; patch 7, window <= 21, FP32)."""
+    LAYOUT_PAIR (two adjacent pixels per CTA; patch 7, window <= 21, FP32).  solver: SOLVER_ADMM
+    (Algorithm 1) or SOLVER_IRLS (the surrogate of Eq. 2 with irls_eps, exactly `iters` steps)."""
     import torch
     H, W = image.shape
     _need(image, torch.float32, (H, W), "image")
@@ -326,7 +333,7 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
     if fp64_check:
         obj = torch.empty((H, W), dtype=torch.float64, device=dev)
         kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, precision, init, fp64_check, layout)
+    o = _options(tol, check_every, precision, init, fp64_check, layout, solver, irls_eps)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
@@ -339,7 +346,7 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
 
 def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
                       check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, ctx: Context | None = None,
-                      out=None, iters_used=None, device=0):
+                      out=None, iters_used=None, device=0, solver=SOLVER_ADMM, irls_eps=1e-6):
     """NLEM on HOST buffers (numpy float32 [H, W] or CPU torch tensor, ideally pinned):
     copies in, denoises and copies out inside the library.  Returns the host output."""
     import numpy as np
@@ -354,7 +361,7 @@ def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, bo
     c = ctx or _ctx(torch.device("cuda", device))
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, pin_memory=img_t.is_pinned())
-    o = _options(tol, check_every, precision, init)
+    o = _options(tol, check_every, precision, init, solver=solver, irls_eps=irls_eps)
     ip = ctypes.c_void_p(iters_used.data_ptr()) if iters_used is not None else None
     _check(load_library().nlem_denoise_host(c.handle, ctypes.c_void_p(img_t.data_ptr()), H, W, int(patch),
                                             int(window), float(h), float(rho), int(iters), _Box(*box),

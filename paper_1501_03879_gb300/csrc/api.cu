@@ -54,7 +54,21 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
       return fail(NLEM_ERR_INVALID, "unknown init %d", opt->init);
     if (opt->layout < NLEM_LAYOUT_AUTO || opt->layout > NLEM_LAYOUT_PAIR)
       return fail(NLEM_ERR_INVALID, "unknown layout %d", opt->layout);
+    if (opt->solver != NLEM_SOLVER_ADMM && opt->solver != NLEM_SOLVER_IRLS)
+      return fail(NLEM_ERR_INVALID, "unknown solver %d", opt->solver);
+    if (opt->solver == NLEM_SOLVER_IRLS) {
+      if (!(opt->irls_eps >= 1e-30f) || !finite(opt->irls_eps))
+        return fail(NLEM_ERR_INVALID, "irls_eps must be finite and >= 1e-30 (got %g)", opt->irls_eps);
+      if (opt->tol > 0.f) return fail(NLEM_ERR_INVALID, "IRLS runs a fixed number of steps: tol must be <= 0");
+    }
   }
+  return NLEM_OK;
+}
+
+// Entry points whose kernels run EM-ADMM only.
+int admm_only(const nlem_options* opt, const char* who) {
+  if (opt && opt->solver != NLEM_SOLVER_ADMM)
+    return fail(NLEM_ERR_INVALID, "%s runs EM-ADMM only (solver %d)", who, opt->solver);
   return NLEM_OK;
 }
 
@@ -68,6 +82,8 @@ nlemk::SolveParams make_params(nlem_box box, float rho, int iters, const nlem_op
   p.tol = opt ? opt->tol : 0.f;
   p.check_every = opt ? opt->check_every : 1;
   p.d = d;
+  p.solver = opt ? opt->solver : NLEM_SOLVER_ADMM;
+  p.eps = opt ? opt->irls_eps : 1e-6f;
   return p;
 }
 
@@ -93,6 +109,9 @@ void nlem_options_default(nlem_options* opt) {
   opt->precision = NLEM_PREC_FP32;
   opt->init = NLEM_INIT_WEIGHTED_MEAN;
   opt->fp64_check = 0;
+  opt->layout = NLEM_LAYOUT_AUTO;
+  opt->solver = NLEM_SOLVER_ADMM;
+  opt->irls_eps = 1e-6f;
 }
 
 const char* nlem_last_error(void) { return g_err.c_str(); }
@@ -154,6 +173,7 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
                    void* stream) {
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
+  if ((rc = admm_only(opt, "em_solve_batch"))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
   if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
@@ -197,6 +217,7 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
                         void* stream) {
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
+  if ((rc = admm_only(opt, "em_solve_batch_host"))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
   if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
@@ -358,7 +379,7 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   }
   int e = nlemk::launch_nlem_fp32(L);
   if (e == -1 && L.layout == NLEM_LAYOUT_PAIR)
-    return fail(NLEM_ERR_UNSUPPORTED, "the pair layout takes FP32, patch 7 and window <= 21 (got patch %d, window %d)",
+    return fail(NLEM_ERR_UNSUPPORTED, "the pair layout takes EM-ADMM in FP32, patch 7 and window <= 21 (got patch %d, window %d)",
                 patch, window);
   if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for patch %d, window %d", patch, window);
   if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise launch");
@@ -557,6 +578,7 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
                        const nlem_options* opt, void* stream) {
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
+  if ((rc = admm_only(opt, "nlem_denoise_batch"))) return rc;
   if (count < 0) return fail(NLEM_ERR_INVALID, "count must be >= 0");
   if (count == 0) return NLEM_OK;
   if (!images) return fail(NLEM_ERR_INVALID, "images is NULL");

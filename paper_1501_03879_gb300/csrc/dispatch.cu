@@ -28,6 +28,7 @@ int launch_em_batch(const EmLaunch& L) {
 }
 
 int launch_nlem_fp32(const NlemLaunch& L) {
+  if (L.prm.solver == 1) return L.layout == 2 ? -1 : launch_nlem_irls(L);   // the pair kernel is ADMM only
   if (L.layout == 2) return launch_nlem_pair_k7(L);
   // windows of more than 256 points (17x17 and up): the pixel-pair kernel; smaller windows run
   // the three-CTAs-per-SM pixel shape

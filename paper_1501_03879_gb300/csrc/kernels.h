@@ -62,6 +62,8 @@ int launch_bf16_weights(const float* img, int H, int W, int pitch, int patch, in
 // Return cudaError_t codes (0 = launched), or -1 when no compiled shape holds the problem.
 int launch_em_batch(const EmLaunch& L);
 int launch_nlem_fp32(const NlemLaunch& L);
+// NLEM-IRLS (L.prm.solver == 1) on the one-pixel kernel, patch 5, 7 or 9.
+int launch_nlem_irls(const NlemLaunch& L);
 // The pixel-pair kernel (7x7 patches, window <= 21, plain FP32 NLEM over the whole image).
 bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);

@@ -52,8 +52,9 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
   if (!std::isfinite(box.lo) || !std::isfinite(box.hi) || box.lo > box.hi)
     return nerr(NLEM_ERR_INVALID, "box must satisfy lo <= hi, both finite");
   if (opt && (opt->check_every < 1 || !std::isfinite(opt->tol) || opt->precision != NLEM_PREC_FP32 ||
-              (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH)))
-    return nerr(NLEM_ERR_INVALID, "options: check_every >= 1, finite tol, FP32 precision, known init");
+              (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH) ||
+              opt->solver != NLEM_SOLVER_ADMM))
+    return nerr(NLEM_ERR_INVALID, "options: check_every >= 1, finite tol, FP32 precision, known init, EM-ADMM");
 
   // descriptors on the stack: this entry point makes no heap or device allocation of its own
   nlemk::BatchImage host[NLEM_NOALLOC_MAX_IMAGES];

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "admm_core.cuh"
+#include "irls_core.cuh"
 #include "kernels.h"
 
 namespace nlemk {
@@ -115,8 +116,9 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
 // One NLEM pixel (Sec. 3, Eq. L1regression) solved by the whole CTA: tile of the
 // reflect-padded image around the clipped search window -> patch rows in shared memory ->
 // weights exp(-||P_i-P_j||^2/h^2) -> start point -> EM-ADMM -> centre coordinate.
-// Ends with a barrier, so the caller may start the next pixel at once.
-template <class C, int K>
+// IRLS: the surrogate solver of Eq. 2 in place of EM-ADMM (NLEM-IRLS, the comparison method of
+// Sec. 3).  Ends with a barrier, so the caller may start the next pixel at once.
+template <class C, int K, bool IRLS = false>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
@@ -207,7 +209,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
       float w = j < n ? expf(-Dp * inv_h2) : 0.f;
       if (wtab) w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;   // precomputed (BF16 mode)
       wreg[p] = w;
-      if (g == 0) sm.lam[j] = w * pp.inv_mu;
+      if (g == 0) sm.lam[j] = IRLS ? w : w * pp.inv_mu;
     }
   }
   if (ex.x0) {   // caller's start point, projected onto C
@@ -235,7 +237,10 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
     __syncthreads();   // lam visible, tile no longer needed (wred aliases it)
     weighted_mean_start<C>(sm, wreg, n, C::D, pp);
   }
-  admm_iterate<C>(sm, n, C::D, pp);
+  if constexpr (IRLS)
+    irls_iterate<C>(sm, n, C::D, pp);
+  else
+    admm_iterate<C>(sm, n, C::D, pp);
   if (ex.z_out) {
     for (int q = t; q < C::D; q += C::NT)
       ex.z_out[pix * (long long)C::D + q] = sm.zv[(q / C::Q) * C::QA + (q % C::Q)];
@@ -267,7 +272,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   __syncthreads();
 }
 
-template <class C, int K>
+template <class C, int K, bool IRLS = false>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
@@ -279,7 +284,7 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
   const long long items = pix_list ? *n_list : (long long)H * W;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const long long pix = pix_list ? (long long)pix_list[it] : it;
-    nlem_pixel<C, K>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
+    nlem_pixel<C, K, IRLS>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
                      wtab, ex);
   }
 }
@@ -301,10 +306,10 @@ inline int launch_em(const EmLaunch& L, int grid_mult) {
   return (int)cudaGetLastError();
 }
 
-template <class C, int K>
+template <class C, int K, bool IRLS = false>
 inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
   if ((L.S + K - 1) * (L.S + K - 1) > C::SZ_WRED) return -1;   // tile must fit its region
-  auto kern = nlem_kernel<C, K>;
+  auto kern = nlem_kernel<C, K, IRLS>;
   const size_t smem = C::SMEM_BYTES;
   if (smem > 232448) return -1;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

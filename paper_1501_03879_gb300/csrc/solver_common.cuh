@@ -16,6 +16,8 @@ struct SolveParams {
   float tol;           // <= 0: fixed count
   int check_every;     // residual check period
   int d;               // runtime dimension (used when D == 0)
+  int solver;          // 0 = EM-ADMM (Algorithm 1), 1 = IRLS on the surrogate of Eq. 2
+  float eps;           // IRLS smoothing epsilon of Eq. 2
 };
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {

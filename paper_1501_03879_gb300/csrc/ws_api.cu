@@ -415,8 +415,8 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
   if (!out) return wfail(NLEM_ERR_INVALID, "out is NULL");
   if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0 || !(box.lo <= box.hi))
     return wfail(NLEM_ERR_INVALID, "rho > 0, iters >= 0 and lo <= hi are required");
-  if (opt && (opt->check_every < 1 || opt->precision != NLEM_PREC_FP32))
-    return wfail(NLEM_ERR_INVALID, "options: check_every >= 1 and FP32 precision");
+  if (opt && (opt->check_every < 1 || opt->precision != NLEM_PREC_FP32 || opt->solver != NLEM_SOLVER_ADMM))
+    return wfail(NLEM_ERR_INVALID, "options: check_every >= 1, FP32 precision and the EM-ADMM solver");
   if (pixels && npix < 0) return wfail(NLEM_ERR_INVALID, "npix must be >= 0");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -451,6 +451,7 @@ int nlem_denoise_warm(nlem_ctx* ctx, nlem_warmstart* ws, const float* image, int
   if (!ws || !out || !iters_used) return wfail(NLEM_ERR_INVALID, "ws, out and iters_used must be non-NULL");
   if (ws->m.d != patch * patch) return wfail(NLEM_ERR_INVALID, "model is for d = %d, patch gives %d", ws->m.d, patch * patch);
   if (!opt || !(opt->tol > 0.f)) return wfail(NLEM_ERR_INVALID, "the warm start needs a tolerance (opt->tol > 0)");
+  if (opt->solver != NLEM_SOLVER_ADMM) return wfail(NLEM_ERR_INVALID, "the warm start runs EM-ADMM only");
   if (!(rho_fallback > 0.f) || iters < 1 || !(box.lo <= box.hi)) return wfail(NLEM_ERR_INVALID, "bad rho, iters or box");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;

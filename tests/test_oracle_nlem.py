@@ -115,3 +115,62 @@ def test_pixel_subset_matches_full():
     pix = [0, 21, 399, 200]
     sub = oracle.nlem(g, 5, 7, 200.0, 1.0, 15, pixels=pix)
     assert np.array_equal(sub["out"], full["out"].reshape(-1)[pix])
+
+
+# ---------------------------------------------------------------------------------------
+# NLEM-IRLS (the comparison method of Sec. 3): IRLS on the surrogate of Eq. 2 per pixel
+# ---------------------------------------------------------------------------------------
+
+def test_nlem_irls_patch_one_reaches_weighted_median():
+    """k = 1: each problem is a weighted scalar median of the window's pixel values.  The
+    surrogate's minimiser is within sum_k w_k sqrt(eps) of problem (1)'s optimum in objective."""
+    g, _ = synth.noisy_image(27, 12, 11, 20.0)
+    H, W = g.shape
+    S, h, eps = 5, 60.0, 1e-6
+    pix = list(range(0, H * W, 5))
+    r = oracle.nlem_irls(g, 1, S, h, eps, 3000, pixels=pix)
+    R = 2
+    for m, lin in enumerate(pix):
+        i, j = divmod(lin, W)
+        vals = g[max(0, i - R):i + R + 1, max(0, j - R):j + R + 1].astype(np.float64).reshape(-1)
+        w = np.exp(-(vals - float(g[i, j])) ** 2 / h ** 2)
+        F = lambda t: float(np.sum(w * np.abs(t - vals)))
+        Fstar = min(F(t) for t in np.clip(vals, 0, 255))
+        assert F(r["out"][m]) <= Fstar + w.sum() * np.sqrt(eps) + 1e-9 * Fstar
+        assert abs(r["obj"][m] - F(r["out"][m])) <= 1e-9 * max(1.0, Fstar)
+
+
+def test_nlem_irls_constant_image_and_zero_steps():
+    for c in (0.0, 91.0, 255.0):
+        g = np.full((9, 10), c, dtype=np.float32)
+        assert np.allclose(oracle.nlem_irls(g, 3, 5, 100.0, 1e-6, 6)["out"], c, atol=1e-9)
+    g = np.full((9, 9), 300.0, dtype=np.float32)
+    assert np.allclose(oracle.nlem_irls(g, 3, 5, 100.0, 1e-6, 6)["out"], 255.0)
+    # zero steps: the start point of the NLEM driver (weighted mean, or the clamped noisy pixel)
+    g, _ = synth.noisy_image(28, 13, 12, 30.0)
+    r0 = oracle.nlem_irls(g, 5, 7, 300.0, 1e-6, 0)
+    assert np.allclose(r0["out"], oracle.nlem(g, 5, 7, 300.0, 1.0, 0)["out"], rtol=0, atol=1e-9)
+    assert np.all(r0["step"] == 0.0)
+    r1 = oracle.nlem_irls(g, 5, 7, 300.0, 1e-6, 0, init_mode=1)
+    assert np.allclose(r1["out"], np.clip(g, 0, 255), atol=0)
+
+
+def test_nlem_irls_last_step_and_monotone_surrogate():
+    """The reported step is ||x(T) - x(T-1)|| / ||x(T)|| of the T-step run, and the surrogate of
+    Eq. 2 does not increase from T-1 to T steps (IRLS is a majorise-minimise scheme; the box
+    projection keeps that because the quadratic majoriser is separable per coordinate)."""
+    g, _ = synth.noisy_image(29, 14, 14, 40.0)
+    k, S, h, eps = 5, 9, 400.0, 1e-6
+    lin = 5 * 14 + 8
+    pts, w, pc = oracle.nlem_problem(g, k, S, h, lin)
+    x0 = oracle.project_box(pc, 0.0, 255.0)
+    sur = lambda x: float(np.sum(w * np.sqrt(np.sum((x - pts) ** 2, 1) + eps)))
+    prev = sur(x0)
+    for T in (1, 2, 3, 5):
+        r = oracle.nlem_irls(g, k, S, h, eps, T, init_mode=1, pixels=[lin])
+        xa, _ = oracle.irls(pts, w, 0.0, 255.0, x0, eps, T - 1)
+        xb, _ = oracle.irls(pts, w, 0.0, 255.0, x0, eps, T)
+        assert r["out"][0] == xb[(k * k - 1) // 2]
+        assert np.isclose(r["step"][0], np.linalg.norm(xb - xa) / np.linalg.norm(xb), rtol=1e-12)
+        assert sur(xb) <= prev + 1e-12 * prev
+        prev = sur(xb)
