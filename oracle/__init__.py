@@ -267,14 +267,16 @@ def nlem_irls(img, k, S, h, eps, iters, lo=0.0, hi=255.0, init_mode=0, pixels=No
     the surrogate of Eq. 2 (irls, projected onto [lo, hi]^d after every step) for exactly `iters`
     steps, from P_C(weighted mean) (init_mode 0) or the projected noisy patch (init_mode 1).
     Pure composition of nlem_problem, weighted_mean_start, project_box, irls and objective.
-    Returns dict(out, step, obj) of float64 arrays: the centre coordinate of x(T),
-    ||x(T) - x(T-1)|| / ||x(T)|| (0 when iters == 0) and the objective of problem (1) at x(T)."""
+    Returns dict(out, step, obj, wsum) of float64 arrays: the centre coordinate of x(T),
+    ||x(T) - x(T-1)|| / ||x(T)|| (0 when iters == 0), the objective of problem (1) at x(T) and the
+    sum of the weights."""
     img = np.ascontiguousarray(img, dtype=np.float32)
     H, W = img.shape
     lins = np.arange(H * W) if pixels is None else np.asarray(pixels, dtype=np.int64).reshape(-1)
     out = np.empty(lins.size)
     step = np.zeros(lins.size)
     obj = np.empty(lins.size)
+    wsum = np.empty(lins.size)
     c = (k * k - 1) // 2
     for i, lin in enumerate(lins):
         pts, w, pc = nlem_problem(img, k, S, h, int(lin))
@@ -285,9 +287,10 @@ def nlem_irls(img, k, S, h, eps, iters, lo=0.0, hi=255.0, init_mode=0, pixels=No
             step[i] = np.linalg.norm(x - xp) / max(np.linalg.norm(x), 1e-300)
         out[i] = x[c]
         obj[i] = objective(x, pts, w)
+        wsum[i] = float(np.sum(w))
     if pixels is None:
-        out, step, obj = out.reshape(H, W), step.reshape(H, W), obj.reshape(H, W)
-    return dict(out=out, step=step, obj=obj)
+        out, step, obj, wsum = (a.reshape(H, W) for a in (out, step, obj, wsum))
+    return dict(out=out, step=step, obj=obj, wsum=wsum)
 
 
 def features(pts, w):

@@ -51,11 +51,13 @@ def test_irls_all_pixels_against_oracle(nl, k, S, H, W, init, T):
     err = rel_err(r["out"].cpu().numpy(), ref["out"])
     assert err.max() <= TOL, err.max()
     assert np.all(r["iters_used"].cpu().numpy() == T)
-    # the last relative step, and the FP64 objective of problem (1) at the GPU's x(T)
+    # the last relative step, and the FP64 objective of problem (1) at the GPU's x(T).  After a few
+    # steps x(T) is not a minimiser, so the objective moves to first order with x: F is Lipschitz
+    # with constant sum_k w_k, and ||x_gpu - x_ref|| <= sqrt(d) * TOL * 255 under the tolerance above.
     st = r["residual"].cpu().numpy().astype(np.float64)
     assert np.all(np.abs(st - ref["step"]) <= 1e-3 * ref["step"] + 2e-6), np.max(np.abs(st - ref["step"]))
     ob = r["obj64"].cpu().numpy()
-    assert np.all(np.abs(ob - ref["obj"]) <= 1e-5 * ref["obj"] + 1e-6)
+    assert np.all(np.abs(ob - ref["obj"]) <= ref["wsum"] * k * TOL * 255.0)
 
 
 def test_irls_other_eps_and_zero_steps(nl):
