@@ -89,7 +89,7 @@ int nlem_ctx_destroy(nlem_ctx* ctx);
  * P_C(weighted mean), run for exactly `iters` iterations.
  *   points  [n][d] float32, row-major (device)      weights [n] float32 >= 0 (device)
  *   x_out   [d] float32 (device)
- * Errors: -1 if n < 1, d < 1 or d > 128, rho <= 0 or not finite, iters < 0, lo > hi or not
+ * Errors: -1 if n < 1, d < 1 or d > 148, rho <= 0 or not finite, iters < 0, lo > hi or not
  * finite.  Points or weights that are not finite, or negative weights, give x_out = NaN.
  * iters == 0 returns P_C(weighted mean).
  */
@@ -112,7 +112,7 @@ int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, in
  *            the projected-gradient optimality residual ||z - P_C(z - g/sum w)||, both in FP64.
  * Errors as em_solve; -5 if n exceeds the largest problem the on-chip (register + shared
  * memory) kernels hold for this d: 896 points for d = 25 and 49, 448 for d = 81, and for other
- * d <= 28 / 60 / 120: 512 / 256 / 256.  B == 0 returns 0 at once (the buffers may then be NULL).
+ * d <= 28 / 60 / 120 / 148: 512 / 256 / 256 / 256.  B == 0 returns 0 at once (the buffers may then be NULL).
  */
 int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n,
                    int d, nlem_box box, float rho, int iters, const float* x0,
@@ -173,6 +173,23 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
                  int window, float h, float rho, int iters, nlem_box box,
                  const nlem_options* opt, float* out, int* iters_used, float* residual,
                  double* obj64, double* kkt64, void* stream);
+
+/*
+ * nlem_denoise_color - NLEM of Sec. 3 on a multichannel image.  The patch of pixel j stacks the
+ * channels' patch x patch patches (coordinate q = c*patch^2 + r*patch + s, d = channels*patch^2),
+ * so ||P_i - P_j||^2 sums over all channels and C = [box.lo, box.hi]^d; otherwise as
+ * nlem_denoise (reflect padding, clipped windows, weights, start, EM-ADMM, stopping rule).
+ *   image [channels][H][pitch] float32 (device), channel planes H*pitch elements apart
+ *   out   [channels][H][W] float32 (device): the centre coordinate of each channel
+ *   iters_used, residual [H][W] or NULL; obj64 / kkt64 [H][W] or NULL (opt->fp64_check)
+ * One pixel per CTA, FP32 weights, EM-ADMM.  Compiled for 3 channels with patch 5 (d = 75,
+ * windows up to 21) and patch 7 (d = 147, windows up to 15: 256 points).
+ * Errors: as nlem_denoise; -5 for other channel counts or patches, larger windows, BF16
+ * precision or the pair layout; -1 for the IRLS solver.
+ */
+int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int channels, int patch,
+                       int window, float h, float rho, int iters, nlem_box box, const nlem_options* opt, float* out,
+                       int* iters_used, float* residual, double* obj64, double* kkt64, void* stream);
 
 /*
  * nlem_denoise_host - nlem_denoise on HOST buffers: copies image_host [H][W] to the device,

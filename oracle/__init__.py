@@ -32,6 +32,8 @@ PINS = {
     "residuals": "r_pri / r_dual against their definitions on stored iterates (step-by-step replay)",
     "nlem": "patch/weight assembly against numpy.pad reflect; constant image; S=1; k=1 weighted median",
     "irls": "surrogate stationarity; converges to the EM within sqrt(eps)-scale",
+    "nlem_color": "identical channels equal grayscale NLEM at h/sqrt(C), mu*sqrt(C); one varying channel "
+                  "beside constant ones equals grayscale NLEM; channel permutation; constant image",
     "nlem_irls": "k=1 windows: the weighted median of the window's pixels after many steps; constant "
                  "image; one pixel equals irls on nlem_problem; zero steps give the start point",
     "weiszfeld": "objective non-increasing; agrees with ADMM at convergence",
@@ -291,6 +293,35 @@ def nlem_irls(img, k, S, h, eps, iters, lo=0.0, hi=255.0, init_mode=0, pixels=No
     if pixels is None:
         out, step, obj, wsum = (a.reshape(H, W) for a in (out, step, obj, wsum))
     return dict(out=out, step=step, obj=obj, wsum=wsum)
+
+
+def nlem_color(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init_mode=0, pixels=None):
+    """NLEM (Sec. 3) on a planar multichannel image [C, H, W]: the patch of a pixel stacks the
+    channels' k x k patches (coordinate c*k*k + r*k + s), so ||P_i - P_j||^2 sums over the channels
+    and w_ij = exp(-sum_c D_c / h^2) is the product of the channels' weights.  Each pixel's problem
+    is solved by Algorithm 1 (em_admm) from P_C(weighted mean) (init_mode 0) or the projected noisy
+    patch (1).  Pure composition of nlem_problem, project_box and em_admm.
+    Returns dict(out [C, ...], iters_used, r_pri, r_dual) per listed pixel."""
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    C, H, W = img.shape
+    lins = np.arange(H * W) if pixels is None else np.asarray(pixels, dtype=np.int64).reshape(-1)
+    out = np.empty((C, lins.size))
+    used = np.zeros(lins.size, dtype=np.int64)
+    rp = np.zeros(lins.size)
+    rd = np.zeros(lins.size)
+    kk = k * k
+    for i, lin in enumerate(lins):
+        parts = [nlem_problem(img[c], k, S, h, int(lin)) for c in range(C)]
+        pts = np.hstack([p[0] for p in parts])
+        w = np.prod(np.stack([p[1] for p in parts]), axis=0)
+        pc = np.concatenate([p[2] for p in parts])
+        z0 = None if init_mode == 0 else project_box(pc, lo, hi)
+        z, used[i], rp[i], rd[i] = em_admm(pts, w, lo, hi, mu, iters, z0=z0, tol=tol, check_every=check_every)
+        out[:, i] = z[np.arange(C) * kk + (kk - 1) // 2]
+    if pixels is None:
+        out = out.reshape(C, H, W)
+        used, rp, rd = used.reshape(H, W), rp.reshape(H, W), rd.reshape(H, W)
+    return dict(out=out, iters_used=used, r_pri=rp, r_dual=rd)
 
 
 def features(pts, w):

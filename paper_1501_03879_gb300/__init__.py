@@ -34,6 +34,7 @@ from ._binding import (  # noqa: F401
     nlem_denoise,
     nlem_denoise_batch,
     nlem_denoise_batch_noalloc,
+    nlem_denoise_color,
     nlem_denoise_ex,
     nlem_denoise_host,
     nlem_device_status,

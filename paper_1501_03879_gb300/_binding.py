@@ -74,6 +74,8 @@ def load_library():
         lib.nlem_denoise.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp, vp,
                                      vp, vp]
         lib.nlem_denoise_host.argtypes = [vp, vp, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.nlem_denoise_color.argtypes = [vp, vp, i, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp,
+                                           vp, vp, vp, vp]
         lib.em_solve_batch_host.argtypes = [vp, vp, vp, ll, i, i, _Box, f, i, vp, ctypes.POINTER(_Options), ll, vp,
                                             vp, vp, vp]
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
@@ -338,6 +340,43 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
     _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
                                        _ptr(obj), _ptr(kkt), _stream(dev)))
+    r = dict(out=o_img, iters_used=used, residual=resid)
+    if fp64_check:
+        r.update(obj64=obj, kkt64=kkt)
+    return r
+
+
+def nlem_denoise_color(image, patch=5, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
+                       check_every=1, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None, out=None):
+    """NLEM (Sec. 3) of a planar multichannel float32 CUDA image [C, H, W] (contiguous): the patches stack
+    the channels.  Returns dict(out [C, H, W], iters_used [H, W], residual [H, W][, obj64, kkt64])."""
+    import torch
+    if not isinstance(image, torch.Tensor) or not image.is_cuda or image.dim() != 3:
+        raise ValueError("device tensor [C, H, W] required")
+    C, H, W = image.shape
+    _need(image, torch.float32, (C, H, W), "image")
+    if not image.is_contiguous():
+        raise ValueError("image must be contiguous [C, H, W]")
+    c = ctx or _ctx(image.device)
+    dev = image.device
+    res = out or {}
+    o_img = res.get("out")
+    if o_img is None:
+        o_img = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty((H, W), dtype=torch.int32, device=dev)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.empty((H, W), dtype=torch.float32, device=dev)
+    obj = kkt = None
+    if fp64_check:
+        obj = torch.empty((H, W), dtype=torch.float64, device=dev)
+        kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
+    o = _options(tol, check_every, PREC_FP32, init, fp64_check)
+    _check(load_library().nlem_denoise_color(c.handle, _ptr(image), H, W, W, C, int(patch), int(window), float(h),
+                                             float(rho), int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img),
+                                             _ptr(used), _ptr(resid), _ptr(obj), _ptr(kkt), _stream(dev)))
     r = dict(out=o_img, iters_used=used, residual=resid)
     if fp64_check:
         r.update(obj64=obj, kkt64=kkt)

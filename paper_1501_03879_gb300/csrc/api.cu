@@ -176,11 +176,11 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
   if ((rc = admm_only(opt, "em_solve_batch"))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
-  if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
+  if (d < 1 || d > 148) return fail(NLEM_ERR_INVALID, "d must be in [1, 148] (got %d)", d);
   if (B == 0) return NLEM_OK;   // an empty batch may pass NULL buffers
   if (!points || !weights || !x_out) return fail(NLEM_ERR_INVALID, "points, weights and x_out must be non-NULL");
-  if (d > 120 || n > nlemk::em_capacity(d))
-    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d, d <= 120)", n,
+  if (n > nlemk::em_capacity(d))
+    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d)", n,
                 d, nlemk::em_capacity(d));
   if ((rc = set_device(ctx))) return rc;
   nlemk::EmLaunch L;
@@ -220,13 +220,13 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
   if ((rc = admm_only(opt, "em_solve_batch_host"))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
-  if (d < 1 || d > 128) return fail(NLEM_ERR_INVALID, "d must be in [1, 128] (got %d)", d);
+  if (d < 1 || d > 148) return fail(NLEM_ERR_INVALID, "d must be in [1, 148] (got %d)", d);
   if (chunk < 0) return fail(NLEM_ERR_INVALID, "chunk must be >= 0 (got %lld)", chunk);
   if (B == 0) return NLEM_OK;   // an empty batch may pass NULL buffers
   if (!points_host || !weights_host || !x_out_host)
     return fail(NLEM_ERR_INVALID, "points_host, weights_host and x_out_host must be non-NULL");
-  if (d > 120 || n > nlemk::em_capacity(d))
-    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d, d <= 120)", n,
+  if (n > nlemk::em_capacity(d))
+    return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d)", n,
                 d, nlemk::em_capacity(d));
   if ((rc = set_device(ctx))) return rc;
   const size_t pb = (size_t)n * d * sizeof(float);   // one problem's points
@@ -383,6 +383,59 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
                 patch, window);
   if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for patch %d, window %d", patch, window);
   if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise launch");
+  return NLEM_OK;
+}
+
+int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int channels, int patch,
+                       int window, float h, float rho, int iters, nlem_box box, const nlem_options* opt, float* out,
+                       int* iters_used, float* residual, double* obj64, double* kkt64, void* stream) {
+  int rc = check_common(ctx, box, rho, iters, opt);
+  if (rc) return rc;
+  if ((rc = admm_only(opt, "nlem_denoise_color"))) return rc;
+  if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1 (got %dx%d)", H, W);
+  if (pitch < W) return fail(NLEM_ERR_INVALID, "pitch %d < W %d", pitch, W);
+  if (channels < 1) return fail(NLEM_ERR_INVALID, "channels must be >= 1 (got %d)", channels);
+  if (patch < 1 || (patch % 2) == 0) return fail(NLEM_ERR_INVALID, "patch must be odd and >= 1 (got %d)", patch);
+  if (window < 1 || (window % 2) == 0) return fail(NLEM_ERR_INVALID, "window must be odd and >= 1 (got %d)", window);
+  if (patch > (H < W ? H : W)) return fail(NLEM_ERR_INVALID, "patch %d exceeds the image side", patch);
+  if (!(h > 0.f) || !finite(h)) return fail(NLEM_ERR_INVALID, "h must be finite and > 0 (got %g)", h);
+  if (!image || !out) return fail(NLEM_ERR_INVALID, "image and out must be non-NULL");
+  if (opt && opt->precision != NLEM_PREC_FP32)
+    return fail(NLEM_ERR_UNSUPPORTED, "multichannel NLEM computes its weights in FP32 only");
+  if (opt && opt->layout == NLEM_LAYOUT_PAIR)
+    return fail(NLEM_ERR_UNSUPPORTED, "multichannel NLEM runs one pixel per CTA");
+  const int cap = nlemk::nlem_color_capacity(channels, patch);
+  if (cap == 0) return fail(NLEM_ERR_UNSUPPORTED, "%d channels with patch %d not compiled (3 channels, patch 5 or 7)",
+                            channels, patch);
+  if (window * window > cap)
+    return fail(NLEM_ERR_UNSUPPORTED, "window %d holds %d points; the %d-channel patch-%d kernel holds %d", window,
+                window * window, channels, patch, cap);
+  if ((rc = set_device(ctx))) return rc;
+  nlemk::NlemColorLaunch L;
+  L.img = image;
+  L.H = H;
+  L.W = W;
+  L.pitch = pitch;
+  L.cstride = (long long)H * pitch;
+  L.channels = channels;
+  L.patch = patch;
+  L.S = window;
+  L.inv_h2 = 1.f / (h * h);
+  L.inv_h2_exact = 1.0 / ((double)h * (double)h);
+  L.prm = make_params(box, rho, iters, opt, channels * patch * patch);
+  L.init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
+  L.out = out;
+  L.iters_used = iters_used;
+  L.resid = residual;
+  const bool chk = opt && opt->fp64_check;
+  L.obj64 = chk ? obj64 : nullptr;
+  L.kkt64 = chk ? kkt64 : nullptr;
+  L.sm_count = ctx->sm_count;
+  L.stream = (cudaStream_t)stream;
+  const int e = nlemk::launch_nlem_color(L);
+  if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for %d channels, patch %d, window %d", channels,
+                           patch, window);
+  if (e != 0) return cuda_fail((cudaError_t)e, "nlem_denoise_color launch");
   return NLEM_OK;
 }
 

@@ -10,6 +10,7 @@ int em_capacity(int d) {
   if (d <= 28) return G28_4::CAP;
   if (d <= 60) return G60_4::CAP;
   if (d <= 120) return G120_4::CAP;
+  if (d <= 148) return G148_4::CAP;
   return 0;
 }
 

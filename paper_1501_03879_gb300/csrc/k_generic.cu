@@ -1,4 +1,4 @@
-// Kernel instances for any other d <= 120 (runtime dimension, zero-filled layout).
+// Kernel instances for any other d <= 148 (runtime dimension, zero-filled layout).
 #include "shapes.h"
 #include "solve_kernels.cuh"
 
@@ -18,6 +18,11 @@ int launch_em_generic(const EmLaunch& L) {
   if (d <= 120) {
     if (n <= G120_2::CAP) return launch_em<G120_2>(L, gm);
     if (n <= G120_4::CAP) return launch_em<G120_4>(L, gm);
+    return -1;
+  }
+  if (d <= 148) {
+    if (n <= G148_2::CAP) return launch_em<G148_2>(L, gm);
+    if (n <= G148_4::CAP) return launch_em<G148_4>(L, gm);
     return -1;
   }
   return -1;

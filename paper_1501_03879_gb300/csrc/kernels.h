@@ -52,6 +52,25 @@ struct NlemLaunch {
   cudaStream_t stream;
 };
 
+// Multichannel NLEM: planar image, channel c at img + c*cstride, out [channels][H][W].
+struct NlemColorLaunch {
+  const float* img;
+  int H, W, pitch;
+  long long cstride;     // elements between channel planes
+  int channels, patch, S;
+  float inv_h2;
+  double inv_h2_exact;
+  SolveParams prm;
+  int init_mode;
+  float* out;
+  int* iters_used;
+  float* resid;
+  double* obj64;
+  double* kkt64;
+  int sm_count;
+  cudaStream_t stream;
+};
+
 // BF16 tensor-core cross terms -> weight table wtab [H*W][S*S]; err set to 1 if an MMA wait
 // ran out.  Returns cudaError_t, or -1 for an uncompiled patch size.
 // wait_tries: bound on the mbarrier polls per tensor-core chunk (0 = the default); issue_mma = 0
@@ -69,6 +88,9 @@ bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
+// Multichannel NLEM (3 channels; patch 5 or 7): the largest window point count, or 0.
+int nlem_color_capacity(int channels, int patch);
+int launch_nlem_color(const NlemColorLaunch& L);
 
 // Warm-start features [item][2 patch^2 + 2] of the listed pixels (or all pixels, row-major);
 // returns cudaError_t, or -1 for an uncompiled patch or a tile larger than 32 x 32.

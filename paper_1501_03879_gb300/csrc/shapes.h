@@ -23,6 +23,8 @@ using G60_1 = Cfg<0, 2, 30, 1, 4>;
 using G60_4 = Cfg<0, 2, 30, 4, 4>;
 using G120_2 = Cfg<0, 4, 30, 2, 8>;
 using G120_4 = Cfg<0, 4, 30, 4, 8>;
+using G148_2 = Cfg<0, 4, 37, 2, 8>;
+using G148_4 = Cfg<0, 4, 37, 4, 8, 1>;     // 217 KB of shared memory: one CTA per SM
 
 int launch_em_d49(const EmLaunch& L);
 int launch_em_d25(const EmLaunch& L);

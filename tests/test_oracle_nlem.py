@@ -174,3 +174,40 @@ def test_nlem_irls_last_step_and_monotone_surrogate():
         assert np.isclose(r["step"][0], np.linalg.norm(xb - xa) / np.linalg.norm(xb), rtol=1e-12)
         assert sur(xb) <= prev + 1e-12 * prev
         prev = sur(xb)
+
+
+# ---------------------------------------------------------------------------------------
+# multichannel NLEM: stacked channel patches (Sec. 3 with colour patches)
+# ---------------------------------------------------------------------------------------
+
+def test_nlem_color_identical_channels_is_grayscale_rescaled():
+    """With C identical channels every distance is C times the grayscale one (w = exp(-D/(h/sqrt C)^2))
+    and every shrink step of Algorithm 1 sees sqrt(C) times the grayscale norm, so the iterates are
+    the grayscale ones at h/sqrt(C) and mu*sqrt(C), block by block (residuals included)."""
+    g, _ = synth.noisy_image(31, 11, 12, 25.0)
+    for C, init, T in ((3, 0, 25), (2, 1, 12)):
+        col = oracle.nlem_color(np.stack([g] * C), 3, 5, 250.0, 0.7, T, init_mode=init, tol=1e-3, check_every=4)
+        gray = oracle.nlem(g, 3, 5, 250.0 / np.sqrt(C), 0.7 * np.sqrt(C), T, init_mode=init, tol=1e-3, check_every=4)
+        for c in range(C):
+            assert np.allclose(col["out"][c], gray["out"], rtol=0, atol=1e-8)
+        assert np.array_equal(col["iters_used"], gray["iters_used"])
+        assert np.allclose(col["r_pri"], gray["r_pri"], rtol=1e-7, atol=1e-12)
+
+
+def test_nlem_color_one_varying_channel_and_permutation():
+    """Constant channels add nothing to the distances, and the solution keeps them at their (in-box)
+    value, so the varying channel's output is grayscale NLEM with the same h and mu.  Permuting the
+    input channels permutes the outputs."""
+    g, _ = synth.noisy_image(32, 10, 13, 20.0)
+    img = np.stack([np.full_like(g, 40.0), g, np.full_like(g, 200.0)])
+    r = oracle.nlem_color(img, 3, 5, 200.0, 1.0, 20)
+    ref = oracle.nlem(g, 3, 5, 200.0, 1.0, 20)
+    assert np.allclose(r["out"][1], ref["out"], rtol=0, atol=1e-8)
+    assert np.allclose(r["out"][0], 40.0, atol=1e-9) and np.allclose(r["out"][2], 200.0, atol=1e-9)
+    h2, _ = synth.noisy_image(33, 10, 13, 30.0)
+    img2 = np.stack([g, h2, np.clip(g + h2 - 100.0, -20.0, 300.0).astype(np.float32)])
+    a = oracle.nlem_color(img2, 3, 5, 300.0, 1.0, 15, pixels=[0, 17, 64, 129])
+    b = oracle.nlem_color(img2[[2, 0, 1]], 3, 5, 300.0, 1.0, 15, pixels=[0, 17, 64, 129])
+    assert np.allclose(b["out"], a["out"][[2, 0, 1]], rtol=0, atol=1e-9)
+    const = oracle.nlem_color(np.stack([np.full_like(g, 7.0), np.full_like(g, 300.0)]), 3, 5, 100.0, 1.0, 10)
+    assert np.allclose(const["out"][0], 7.0) and np.allclose(const["out"][1], 255.0)
