@@ -555,7 +555,8 @@ def extra_convergence(nl, ctx):
 def extra_color(nl, ctx):
     """Multichannel NLEM on a 512x512 three-channel synthetic image (channels f, 0.6 f + 40 and 255 - f
     of one clean image, so that their edges coincide, plus independent noise): 5x5 colour patches
-    (d = 75), 21x21 window, h = 10 sigma sqrt(3), the paper's 4 iterations at mu = 1e-3 from the noisy
+    (d = 75, one CTA per pixel) and 7x7 colour patches (d = 147, each pixel split over a two-CTA
+    cluster), 21x21 window, h = 10 sigma sqrt(3), the paper's 4 iterations at mu = 1e-3 from the noisy
     patch; PSNR over the three channels for NLM and NLEM, and the solver's rate."""
     import torch
     import synth
@@ -563,19 +564,21 @@ def extra_color(nl, ctx):
     f = synth.clean_image(SEED * 10 + 1000, H, W)
     fc = np.stack([f, 0.6 * f + 40.0, 255.0 - f])
     rows = []
+    nmap = window_counts(H, W, S_WIN)
     for si, sg in enumerate((20.0, 40.0)):
         g = np.stack([_noisy_realisation(fc[c], sg, SEED * 1000 + 1000 + 10 * si + c) for c in range(3)])
         img = torch.from_numpy(g).to(dev)
-        kw = dict(patch=5, window=S_WIN, h=10 * sg * math.sqrt(3.0), box=BOX, ctx=ctx)
-        nlm = nl.nlem_denoise_color(img, rho=1.0, iters=0, init=nl.INIT_WEIGHTED_MEAN, **kw)["out"].cpu().numpy()
-        ms, r = _timed(lambda: nl.nlem_denoise_color(img, rho=1e-3, iters=4, init=nl.INIT_NOISY_PATCH, **kw), reps=3)
-        nmap = window_counts(H, W, S_WIN)
-        fl = nlem_flops(nmap, np.full_like(nmap, 4.0), 75)
-        rows.append({"sigma": sg, "psnr_noisy": synth.psnr(g, fc), "psnr_nlm": synth.psnr(nlm, fc),
-                     "psnr_nlem": synth.psnr(r["out"].cpu().numpy(), fc), "mpixel_per_s": H * W / (ms * 1e-3) / 1e6,
-                     "tflops": fl / (ms * 1e-3) / 1e12})
-    return {"workload": f"{H}x{W}x3 synthetic, 5x5 colour patches (d=75), 21x21 window, h=10 sigma sqrt(3), "
-                        "mu=1e-3, 4 iterations, noisy-patch start", "rows": rows}
+        for k in (5, 7):
+            kw = dict(patch=k, window=S_WIN, h=10 * sg * math.sqrt(3.0), box=BOX, ctx=ctx)
+            nlm = nl.nlem_denoise_color(img, rho=1.0, iters=0, init=nl.INIT_WEIGHTED_MEAN, **kw)["out"].cpu().numpy()
+            ms, r = _timed(lambda: nl.nlem_denoise_color(img, rho=1e-3, iters=4, init=nl.INIT_NOISY_PATCH, **kw),
+                           reps=3)
+            fl = nlem_flops(nmap, np.full_like(nmap, 4.0), 3 * k * k)
+            rows.append({"sigma": sg, "patch": k, "psnr_noisy": synth.psnr(g, fc), "psnr_nlm": synth.psnr(nlm, fc),
+                         "psnr_nlem": synth.psnr(r["out"].cpu().numpy(), fc),
+                         "mpixel_per_s": H * W / (ms * 1e-3) / 1e6, "tflops": fl / (ms * 1e-3) / 1e12})
+    return {"workload": f"{H}x{W}x3 synthetic, 5x5 and 7x7 colour patches (d=75, 147), 21x21 window, "
+                        "h=10 sigma sqrt(3), mu=1e-3, 4 iterations, noisy-patch start", "rows": rows}
 
 
 def run_extras(nl, ctx, imgs, args):

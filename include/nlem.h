@@ -182,10 +182,12 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
  *   image [channels][H][pitch] float32 (device), channel planes H*pitch elements apart
  *   out   [channels][H][W] float32 (device): the centre coordinate of each channel
  *   iters_used, residual [H][W] or NULL; obj64 / kkt64 [H][W] or NULL (opt->fp64_check)
- * One pixel per CTA, FP32 weights, EM-ADMM.  Compiled for 3 channels with patch 5 (d = 75,
- * windows up to 21) and patch 7 (d = 147, windows up to 15: 256 points).
+ * FP32 weights, EM-ADMM.  Compiled for 3 channels with patch 5 (d = 75, windows up to 21, one
+ * pixel per CTA) and patch 7 (d = 147, windows up to 21).  With patch 7, windows of more than 256
+ * points split each pixel over a cluster of two CTAs that add their partial sums every iteration
+ * through distributed shared memory; the FP64 check is available up to 256 points (window 15).
  * Errors: as nlem_denoise; -5 for other channel counts or patches, larger windows, BF16
- * precision or the pair layout; -1 for the IRLS solver.
+ * precision, the pair layout or the FP64 check on a split window; -1 for the IRLS solver.
  */
 int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int channels, int patch,
                        int window, float h, float rho, int iters, nlem_box box, const nlem_options* opt, float* out,

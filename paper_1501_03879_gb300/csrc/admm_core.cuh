@@ -154,11 +154,19 @@ __device__ __forceinline__ float4 load_quad(const float* row, int i, bool last) 
   return v;
 }
 
+// Combining the column totals of the CTAs that share one problem.  The default is one CTA per
+// problem: nothing to combine.  A type X with the same static member, called by every thread of
+// the CTA after the block reduction, replaces warp 0's tot0 / tot1 with the totals over its CTAs.
+struct NoExchange {
+  template <class C>
+  __device__ __forceinline__ static void combine(float4&, float4&) {}
+};
+
 // Two-level column reduction of every thread's acc[QR] row over the lanes that share a
 // slice.  Returns, in warp 0, the totals of columns lane and lane+32 (float4 each).
 // Contains one __syncthreads; wred/cred may be reused after the caller's next barrier.
 // Variant for callers that already wrote their row (NQR float4) at wred[(warp*32+lane)*NQR].
-template <class C>
+template <class C, class X = NoExchange>
 __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot0, float4& tot1) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   __syncwarp();
@@ -202,9 +210,10 @@ __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot
       if (lane + 32 < C::COLS) tot1 = f4add(tot1, sm.cred[w * C::COLS + lane + 32]);
     }
   }
+  X::template combine<C>(tot0, tot1);
 }
 
-template <class C>
+template <class C, class X = NoExchange>
 __device__ __forceinline__ void block_reduce(const Smem<C>& sm, const float (&acc)[C::QR],
                                              float4& tot0, float4& tot1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -212,14 +221,14 @@ __device__ __forceinline__ void block_reduce(const Smem<C>& sm, const float (&ac
 #pragma unroll
   for (int i = 0; i < C::NQR; ++i)
     my[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
-  block_reduce_rows<C>(sm, tot0, tot1);
+  block_reduce_rows<C, X>(sm, tot0, tot1);
 }
 
 
 // Weighted sum of the points (sum_j w_j a_j) and sum_j w_j, with w_j = weight of point slot
 // j taken from wreg[p] (0 for inactive slots).  Writes z0 = P_C(sum w a / sum w) into zv and
 // cv (c(0) = z(0)), zeroes sgv.  If sum w == 0 the plain mean of the n points is used.
-template <class C>
+template <class C, class X = NoExchange>
 __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P], int n, int d,
                                     const SolveParams& prm) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31;
@@ -239,7 +248,7 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
       if (g == 0) acc[C::Q] += w;
     }
     float4 t0, t1;
-    block_reduce<C>(sm, acc, t0, t1);
+    block_reduce<C, X>(sm, acc, t0, t1);
     // every lane of warp 0 learns sum w from the column holding slot Q of slice 0
     __shared__ float s_wsum;
     if (t < 32) {
@@ -287,7 +296,7 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
 // lanes of a point split the rsqrt of the step s.  The standalone batch kernel measured 3.6%
 // faster with it; the NLEM kernels of one pixel per CTA measured 2-5% slower, so they do not
 // take it (the register allocation decides).
-template <class C, bool SPLIT = false>
+template <class C, bool SPLIT = false, class X = NoExchange>
 __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm) {
   static_assert(!SPLIT || C::G == 2, "the split rsqrt pairs the two lanes of a point");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
@@ -487,7 +496,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
       }
     }
     float4 t0, t1;
-    block_reduce_rows<C>(sm, t0, t1);
+    block_reduce_rows<C, X>(sm, t0, t1);
     // finalize (warp 0): z+ = P_C(z - sum g / n), c+ = 2 z+ - z, residuals on checks
     if (t < 32) {
       if (SPLIT && t == 0) {   // the next iteration's check flag (read by every thread after the barrier)

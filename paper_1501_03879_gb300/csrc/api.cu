@@ -410,6 +410,9 @@ int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitc
   if (window * window > cap)
     return fail(NLEM_ERR_UNSUPPORTED, "window %d holds %d points; the %d-channel patch-%d kernel holds %d", window,
                 window * window, channels, patch, cap);
+  if (opt && opt->fp64_check && window * window > nlemk::nlem_color_single_cta_capacity(channels, patch))
+    return fail(NLEM_ERR_UNSUPPORTED, "the FP64 check needs the window in one CTA (at most %d points here)",
+                nlemk::nlem_color_single_cta_capacity(channels, patch));
   if ((rc = set_device(ctx))) return rc;
   nlemk::NlemColorLaunch L;
   L.img = image;

@@ -88,8 +88,10 @@ bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
-// Multichannel NLEM (3 channels; patch 5 or 7): the largest window point count, or 0.
+// Multichannel NLEM (3 channels; patch 5 or 7): the largest window point count, or 0; and the
+// largest one CTA holds (larger windows split each pixel over a two-CTA cluster).
 int nlem_color_capacity(int channels, int patch);
+int nlem_color_single_cta_capacity(int channels, int patch);
 int launch_nlem_color(const NlemColorLaunch& L);
 
 // Warm-start features [item][2 patch^2 + 2] of the listed pixels (or all pixels, row-major);
