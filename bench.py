@@ -109,8 +109,8 @@ PROFILED = {
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.13},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "0d3d7b93569d284b", "traffic": (361799168 + 3646976) * 64, "fma_pipe_pct": 41.57,
-                        "issue_pct": 35.43, "smem_wavefront_pct": 66.78},
+    "em_batch_kernel": {"sources": "45234b161c959ca3", "traffic": (361691136 + 3998464) * 64, "fma_pipe_pct": 41.57,
+                        "issue_pct": 35.44, "smem_wavefront_pct": 66.81},
 }
 
 
