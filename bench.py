@@ -20,7 +20,7 @@ At one GPU the line also carries `extras`, each timed on its own after the main 
 rho = 1e-3 on the same images; the Table 1 protocol of Sec. 3 (NLM, NLEM-IRLS and NLEM-ADMM
 PSNR over 10 noise realisations at sigma 10..80, 4 iterations); synthetic analogues of Figs. 1
 and 2 (PSNR and objective against iteration, ADMM vs IRLS); multichannel NLEM on a 512x512x3
-image; BF16 tensor-core weights against
+image; standalone batches over per-coordinate boxes and a ball; BF16 tensor-core weights against
 FP32 on a 1024x1024 image with impulse
 noise; 64 uneven images in one persistent graph-captured launch; and the learned warm start on
 a 2048x2048 image against plain EM-ADMM.  --no-extras skips them.
@@ -581,6 +581,34 @@ def extra_color(nl, ctx):
                         "h=10 sigma sqrt(3), mu=1e-3, 4 iterations, noisy-patch start", "rows": rows}
 
 
+def extra_sets(nl, ctx):
+    """Standalone batches over constraint sets beyond the box: 16384 problems of 256 points in
+    d = 49 (the set kernels' runtime-dimension shape), per-coordinate boxes and a ball that cuts
+    the solutions, rho = 1, 60 iterations; solves/s and the solver's FP32 rate."""
+    import torch
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B, n, d, T = 16384, 256, EM_D, 60
+    pts = torch.empty((B, n, d), device=dev)
+    if not os.path.exists(synth.SYNTH_LIB):
+        synth.build_device_generator()
+    synth.device_em_points(SEED + 17, B, n, d, pts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    w = torch.from_numpy(synth.em_weights(SEED + 17, np.arange(B), n)).to(dev)
+    lo = torch.linspace(0.0, 100.0, d, device=dev)
+    hi = lo + 100.0
+    c = torch.full((d,), 60.0, device=dev)
+    rows = []
+    for name, kw in (("coordinate boxes", dict(lo=lo, hi=hi)), ("ball r=200", dict(center=c, radius=200.0))):
+        ms, _ = _timed(lambda: nl.em_solve_batch_set(pts, w, rho=1.0, iters=T, ctx=ctx, **kw), reps=3)
+        fl = em_flops(np.full(B, T), n, d)
+        rows.append({"set": name, "solves_per_s": B / (ms * 1e-3), "tflops": fl / (ms * 1e-3) / 1e12, "ms": ms})
+    ms, _ = _timed(lambda: nl.em_solve_batch(pts, w, rho=1.0, iters=T, ctx=ctx), reps=3)
+    rows.append({"set": "box (em_solve_batch, d = 49 shape)", "solves_per_s": B / (ms * 1e-3),
+                 "tflops": em_flops(np.full(B, T), n, d) / (ms * 1e-3) / 1e12, "ms": ms})
+    del pts
+    return {"workload": f"{B} problems, n={n}, d={d}, rho=1, {T} iterations", "rows": rows}
+
+
 def run_extras(nl, ctx, imgs, args):
     peaks = {}
     try:
@@ -594,6 +622,7 @@ def run_extras(nl, ctx, imgs, args):
     out["table1"] = extra_table1(nl, ctx)
     out["convergence"] = extra_convergence(nl, ctx)
     out["color"] = extra_color(nl, ctx)
+    out["sets"] = extra_sets(nl, ctx)
     out["bf16"] = extra_mixed_precision(nl, ctx, peaks)
     out["batch"] = extra_batch(nl, ctx)
     out["warm_start"] = extra_warm_start(nl, ctx, args.ws_train)

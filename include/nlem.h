@@ -119,6 +119,33 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
                    const nlem_options* opt, float* x_out, int* iters_used, float* residual,
                    double* obj64, double* kkt64, void* stream);
 
+/* Constraint sets C beyond the box (Algorithm 1 needs only a closed convex C with a simple
+ * projection, Sec. 2).  The arrays are caller-owned DEVICE arrays of d floats. */
+#define NLEM_SET_COORD_BOXES 1      /* prod_q [lo[q], hi[q]] (lo[q] <= hi[q] required) */
+#define NLEM_SET_BALL 2             /* {x : ||x - center||_2 <= radius} */
+
+typedef struct {
+  int kind;              /* NLEM_SET_* */
+  const float* lo;       /* COORD_BOXES: lower bounds [d] */
+  const float* hi;       /* COORD_BOXES: upper bounds [d] */
+  const float* center;   /* BALL: centre [d] */
+  float radius;          /* BALL: finite, >= 0 */
+} nlem_set;
+
+/*
+ * em_solve_batch_set - em_solve_batch with C = *set: the z-update of Algorithm 1 and the start
+ * (x0, or the weighted mean) are projected onto the set instead of the box.  The coordinate
+ * boxes clamp each coordinate; the ball pulls a point outside it radially onto the sphere.
+ *   points, weights, x0, x_out, iters_used, residual: as em_solve_batch.
+ * Runs on the runtime-dimension kernels: d <= 148, n at most 512 (d <= 28) or 256 (d <= 148).
+ * Errors: as em_solve_batch; -1 also for a NULL set, an unknown kind, NULL set arrays, a radius
+ * that is negative or not finite, or the IRLS solver; -5 for n above the capacity or the FP64
+ * check (its optimality residual is the box's).  B == 0 returns 0 at once.
+ */
+int em_solve_batch_set(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n, int d,
+                       const nlem_set* set, float rho, int iters, const float* x0, const nlem_options* opt,
+                       float* x_out, int* iters_used, float* residual, void* stream);
+
 /*
  * em_solve_batch_host - em_solve_batch on HOST buffers, with the copies pipelined against the
  * solves.  The batch runs in chunks of `chunk` problems (0 = about 1 GiB of points per chunk).

@@ -32,6 +32,11 @@ PINS = {
     "residuals": "r_pri / r_dual against their definitions on stored iterates (step-by-step replay)",
     "nlem": "patch/weight assembly against numpy.pad reflect; constant image; S=1; k=1 weighted median",
     "irls": "surrogate stationarity; converges to the EM within sqrt(eps)-scale",
+    "project_set": "per-coordinate boxes: coordinate clamp; ball: brute-force argmin on a 2-D grid, "
+                   "idempotent, interior points fixed",
+    "em_admm_set": "equal bounds reproduce em_admm's box run; d=1 boxes give the clamped weighted median; "
+                   "large ball gives the unconstrained median, radius 0 the centre; 2-D brute-force minimum "
+                   "over the ball and over a box",
     "nlem_color": "identical channels equal grayscale NLEM at h/sqrt(C), mu*sqrt(C); one varying channel "
                   "beside constant ones equals grayscale NLEM; channel permutation; constant image",
     "nlem_irls": "k=1 windows: the weighted median of the window's pixels after many steps; constant "
@@ -70,6 +75,10 @@ def _load():
     lib.orc_prox.argtypes = [D, D, c_double, c_int, D]
     lib.orc_prox_conj.argtypes = [D, D, c_double, c_int, D]
     lib.orc_project_box.argtypes = [D, c_int, c_double, c_double, D]
+    lib.orc_project_set.argtypes = [D, c_int, c_int, D, D, c_double, D]
+    lib.orc_em_admm_set.argtypes = [D, D, c_int, c_int, c_int, D, D, c_double, c_double, c_int, D, c_double, c_int,
+                                    D, ctypes.POINTER(c_int), D, D]
+    lib.orc_em_admm_set.restype = c_int
     lib.orc_objective.argtypes = [D, D, D, c_int, c_int]
     lib.orc_objective.restype = c_double
     lib.orc_kkt_residual.argtypes = [D, D, D, c_int, c_int, c_double, c_double, c_double]
@@ -138,6 +147,40 @@ def project_box(x, lo, hi):
     out = np.empty_like(x)
     _load().orc_project_box(_dp(x), x.size, float(lo), float(hi), _dp(out))
     return out
+
+
+SET_COORD_BOXES = 1
+SET_BALL = 2
+
+
+def project_set(x, kind, a, b=None, r=0.0):
+    """Projection onto per-coordinate boxes prod_q [a_q, b_q] (kind 1) or the ball ||x - a|| <= r
+    (kind 2): the constraint sets beyond the box that problem (1) admits (Sec. 2)."""
+    x, a = _f64(x), _f64(a)
+    b = _f64(b) if b is not None else np.zeros_like(a)
+    out = np.empty_like(x)
+    _load().orc_project_set(_dp(x), x.size, int(kind), _dp(a), _dp(b), float(r), _dp(out))
+    return out
+
+
+def em_admm_set(pts, w, kind, a, b=None, r=0.0, mu=1.0, iters=100, z0=None, tol=0.0, check_every=1):
+    """Algorithm 1 with the z-update projecting onto project_set's set (kind 1 or 2); the start is
+    z0 as given, else the projected weighted mean.  Returns (z, iters_used, r_pri, r_dual)."""
+    pts, w, a = _f64(pts), _f64(w), _f64(a)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    n, d = pts.shape
+    b = _f64(b) if b is not None else np.zeros_like(a)
+    z = np.empty(d)
+    used = np.zeros(1, dtype=np.int32)
+    rp = np.zeros(1)
+    rd = np.zeros(1)
+    z0a = _f64(z0) if z0 is not None else None
+    rc = _load().orc_em_admm_set(_dp(pts), _dp(w), n, d, int(kind), _dp(a), _dp(b), float(r), float(mu), int(iters),
+                                 _dp(z0a), float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd))
+    if rc != 0:
+        raise MemoryError("oracle em_admm_set out of memory")
+    return z, int(used[0]), float(rp[0]), float(rd[0])
 
 
 def objective(z, pts, w):

@@ -169,9 +169,55 @@ void orc_weighted_mean_start(const double *pts, const double *w, int n, int d, d
  * The residuals of the last iteration run are always returned (0 if iters == 0).
  * Returns 0, or -1 if memory runs out.
  * ------------------------------------------------------------------------------------- */
+/* Constraint sets other than the box of Sec. 3 (the method needs only a closed convex C with a
+ * simple projection, Sec. 2).  kind 1: per-coordinate boxes prod_q [pa[q], pb[q]], projected by
+ * clamping each coordinate; kind 2: the ball ||x - pa|| <= r, projected by pulling x radially
+ * onto the sphere when it lies outside.  Any other kind leaves x as it is. */
+void orc_project_set(const double *x, int d, int kind, const double *pa, const double *pb, double r,
+                     double *out) {
+  if (kind == 1) {
+    for (int q = 0; q < d; ++q) {
+      double t = x[q];
+      if (t < pa[q]) t = pa[q];
+      if (t > pb[q]) t = pb[q];
+      out[q] = t;
+    }
+  } else if (kind == 2) {
+    double s = 0.0;
+    for (int q = 0; q < d; ++q) s += (x[q] - pa[q]) * (x[q] - pa[q]);
+    const double nr = sqrt(s);
+    const double f = nr > r ? r / nr : 1.0;
+    for (int q = 0; q < d; ++q) out[q] = pa[q] + f * (x[q] - pa[q]);
+  } else {
+    for (int q = 0; q < d; ++q) out[q] = x[q];
+  }
+}
+
+/* Algorithm 1 with the z-update's projection onto the box [lo, hi]^d (kind 0) or onto the set of
+ * orc_project_set (kind 1, 2); the start is z0 as given, else the weighted mean projected onto C. */
+static int em_admm_impl(const double *pts, const double *w, int n, int d, int kind, double lo, double hi,
+                        const double *pa, const double *pb, double rad, double mu, int iters,
+                        const double *z0, double tol, int check_every, double *z, int *iters_used,
+                        double *rpri, double *rdual);
+
 int orc_em_admm(const double *pts, const double *w, int n, int d, double lo, double hi,
                 double mu, int iters, const double *z0, double tol, int check_every,
                 double *z, int *iters_used, double *rpri, double *rdual) {
+  return em_admm_impl(pts, w, n, d, 0, lo, hi, NULL, NULL, 0.0, mu, iters, z0, tol, check_every, z,
+                      iters_used, rpri, rdual);
+}
+
+int orc_em_admm_set(const double *pts, const double *w, int n, int d, int kind, const double *pa,
+                    const double *pb, double rad, double mu, int iters, const double *z0, double tol,
+                    int check_every, double *z, int *iters_used, double *rpri, double *rdual) {
+  return em_admm_impl(pts, w, n, d, kind, 0.0, 0.0, pa, pb, rad, mu, iters, z0, tol, check_every, z,
+                      iters_used, rpri, rdual);
+}
+
+static int em_admm_impl(const double *pts, const double *w, int n, int d, int kind, double lo, double hi,
+                        const double *pa, const double *pb, double rad, double mu, int iters,
+                        const double *z0, double tol, int check_every, double *z, int *iters_used,
+                        double *rpri, double *rdual) {
   double *x = (double *)malloc(sizeof(double) * (size_t)n * d);
   double *y = (double *)calloc((size_t)n * d, sizeof(double));
   double *r = (double *)malloc(sizeof(double) * (size_t)d);
@@ -183,8 +229,11 @@ int orc_em_admm(const double *pts, const double *w, int n, int d, double lo, dou
   }
   if (z0) {
     for (int q = 0; q < d; ++q) z[q] = z0[q];
-  } else {
+  } else if (kind == 0) {
     orc_weighted_mean_start(pts, w, n, d, lo, hi, z);
+  } else {
+    orc_weighted_mean_start(pts, w, n, d, -INFINITY, INFINITY, z);
+    orc_project_set(z, d, kind, pa, pb, rad, z);
   }
   if (check_every < 1) check_every = 1;
   int t_done = 0;
@@ -202,7 +251,10 @@ int orc_em_admm(const double *pts, const double *w, int n, int d, double lo, dou
       zprev[q] = z[q];
       z[q] = r[q] / (double)n;
     }
-    orc_project_box(z, d, lo, hi, z);
+    if (kind == 0)
+      orc_project_box(z, d, lo, hi, z);
+    else
+      orc_project_set(z, d, kind, pa, pb, rad, z);
     for (int k = 0; k < n; ++k) {
       double *yk = y + (size_t)k * d;
       const double *xk = x + (size_t)k * d;

@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     em_solve,
     em_solve_batch,
     em_solve_batch_host,
+    em_solve_batch_set,
     lib_path,
     load_library,
     nlem_batch_config,

@@ -38,6 +38,11 @@ class _ImageDesc(ctypes.Structure):
                 ("patch", ctypes.c_int), ("window", ctypes.c_int), ("h", ctypes.c_float)]
 
 
+class _Set(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
+                ("center", ctypes.c_void_p), ("radius", ctypes.c_float)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("layout", ctypes.c_int),
@@ -74,6 +79,8 @@ def load_library():
         lib.nlem_denoise.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp, vp,
                                      vp, vp]
         lib.nlem_denoise_host.argtypes = [vp, vp, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.em_solve_batch_set.argtypes = [vp, vp, vp, ll, i, i, ctypes.POINTER(_Set), f, i, vp,
+                                           ctypes.POINTER(_Options), vp, vp, vp, vp]
         lib.nlem_denoise_color.argtypes = [vp, vp, i, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp,
                                            vp, vp, vp, vp]
         lib.em_solve_batch_host.argtypes = [vp, vp, vp, ll, i, i, _Box, f, i, vp, ctypes.POINTER(_Options), ll, vp,
@@ -263,6 +270,48 @@ def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=Non
     if fp64_check:
         r.update(obj64=obj, kkt64=kkt)
     return r
+
+
+SET_COORD_BOXES = 1
+SET_BALL = 2
+
+
+def em_solve_batch_set(points, weights, lo=None, hi=None, center=None, radius=None, rho=1.0, iters=100, x0=None,
+                       tol=0.0, check_every=1, ctx: Context | None = None, out=None):
+    """Algorithm 1 on B problems over a constraint set other than the box: per-coordinate boxes
+    (lo, hi: float32 CUDA [d]) or the ball ||x - center|| <= radius (center: float32 CUDA [d]).
+    Returns dict(x [B,d], iters_used [B] int32, residual [B])."""
+    import torch
+    B, n, d = points.shape
+    _need(points, torch.float32, (B, n, d), "points")
+    _need(weights, torch.float32, (B, n), "weights")
+    if x0 is not None:
+        _need(x0, torch.float32, (B, d), "x0")
+    s = _Set()
+    if center is not None:
+        _need(center, torch.float32, (d,), "center")
+        s.kind, s.center, s.radius = SET_BALL, _ptr(center), float(radius)
+    else:
+        _need(lo, torch.float32, (d,), "lo")
+        _need(hi, torch.float32, (d,), "hi")
+        s.kind, s.lo, s.hi = SET_COORD_BOXES, _ptr(lo), _ptr(hi)
+    c = ctx or _ctx(points.device)
+    dev = points.device
+    res = out or {}
+    x = res.get("x")
+    if x is None:
+        x = torch.empty((B, d), dtype=torch.float32, device=dev)
+    used = res.get("iters_used")
+    if used is None:
+        used = torch.empty(B, dtype=torch.int32, device=dev)
+    resid = res.get("residual")
+    if resid is None:
+        resid = torch.empty(B, dtype=torch.float32, device=dev)
+    o = _options(tol, check_every)
+    _check(load_library().em_solve_batch_set(c.handle, _ptr(points), _ptr(weights), B, n, d, ctypes.byref(s),
+                                             float(rho), int(iters), _ptr(x0), ctypes.byref(o), _ptr(x), _ptr(used),
+                                             _ptr(resid), _stream(dev)))
+    return dict(x=x, iters_used=used, residual=resid)
 
 
 def _host_ptr(t, dtype, shape, name):

@@ -25,6 +25,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "solver_common.cuh"
 
 namespace nlemk {
@@ -225,12 +227,70 @@ __device__ __forceinline__ void block_reduce(const Smem<C>& sm, const float (&ac
 }
 
 
+// Projection onto the constraint set C of problem (1).  ScalarBox is the box [lo, hi]^d of Sec. 3
+// (bounds in SolveParams), clamped per coordinate where each value is formed.  The other sets are
+// projected by warp 0, eight values per lane (the lane's two reduction columns), with their
+// parameters read through the read-only cache.
+struct ScalarBox {};
+struct CoordBoxes {                 // prod_q [lo[q], hi[q]] (device arrays of d floats)
+  const float* lo;
+  const float* hi;
+};
+struct Ball {                       // {x : ||x - c|| <= r} (device array of d floats, r >= 0)
+  const float* c;
+  float r;
+};
+
+// Warp 0: values v[k] of coordinates q[k] (where ok[k]) onto C; every lane of warp 0 calls it.
+__device__ __forceinline__ void project_lane(const CoordBoxes& s, float (&v)[8], const int (&q)[8],
+                                             const bool (&ok)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (ok[k]) v[k] = fminf(fmaxf(v[k], __ldg(s.lo + q[k])), __ldg(s.hi + q[k]));
+}
+__device__ __forceinline__ void project_lane(const Ball& s, float (&v)[8], const int (&q)[8], const bool (&ok)[8]) {
+  float c[8], r2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c[k] = ok[k] ? __ldg(s.c + q[k]) : 0.f;
+    const float e = ok[k] ? v[k] - c[k] : 0.f;
+    r2 = fmaf(e, e, r2);
+  }
+  const float nr = sqrtf(warp_sum(r2));
+  const float scale = nr > s.r ? s.r / nr : 1.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (ok[k]) v[k] = fmaf(v[k] - c[k], scale, c[k]);
+}
+
+// Warp 0: project the vector held in zv (slice layout, phantom slots zero) onto C in place.
+template <class C, class PJ>
+__device__ __forceinline__ void project_zv(const Smem<C>& sm, int d, const PJ& pj) {
+  const int lane = threadIdx.x & 31;
+  float v[8];
+  int q[8];
+  bool ok[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int col = lane + 32 * (k / 4), sg = col / C::NQR, slot = 4 * (col - sg * C::NQR) + (k % 4);
+    ok[k] = col < C::COLS && slot < slice_real<C>(sg, d);
+    q[k] = sg * C::Q + slot;
+    v[k] = ok[k] ? sm.zv[sg * C::QA + slot] : 0.f;
+  }
+  project_lane(pj, v, q, ok);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int col = lane + 32 * (k / 4), sg = col / C::NQR, slot = 4 * (col - sg * C::NQR) + (k % 4);
+    if (ok[k]) sm.zv[sg * C::QA + slot] = v[k];
+  }
+}
+
 // Weighted sum of the points (sum_j w_j a_j) and sum_j w_j, with w_j = weight of point slot
 // j taken from wreg[p] (0 for inactive slots).  Writes z0 = P_C(sum w a / sum w) into zv and
 // cv (c(0) = z(0)), zeroes sgv.  If sum w == 0 the plain mean of the n points is used.
-template <class C, class X = NoExchange>
+template <class C, class X = NoExchange, class PJ = ScalarBox>
 __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P], int n, int d,
-                                    const SolveParams& prm) {
+                                    const SolveParams& prm, const PJ& pj = PJ()) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31;
   const bool last = (g == C::G - 1);
   for (int pass = 0; pass < 2; ++pass) {
@@ -262,6 +322,28 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
       const float wsum = s_wsum;
       if (pass == 0 && !(wsum > 0.f)) {
         // fall through to the unweighted pass (uniform decision across warp 0)
+      } else if constexpr (!std::is_same<PJ, ScalarBox>::value) {
+        const float inv = 1.f / wsum;
+        float v[8];
+        int q[8];
+        bool ok[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int col = lane + 32 * (k / 4), sg = col / C::NQR, slot = 4 * (col - sg * C::NQR) + (k % 4);
+          ok[k] = col < C::COLS && slot < slice_real<C>(sg, d);
+          q[k] = sg * C::Q + slot;
+          v[k] = ok[k] ? f4get(k < 4 ? t0 : t1, k % 4) * inv : 0.f;
+        }
+        project_lane(pj, v, q, ok);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int col = lane + 32 * (k / 4), sg = col / C::NQR, slot = 4 * (col - sg * C::NQR) + (k % 4);
+          if (col < C::COLS && slot < C::QA) {
+            sm.zv[sg * C::QA + slot] = v[k];
+            sm.cv[sg * C::QA + slot] = v[k];
+            sm.sgv[sg * C::QA + slot] = 0.f;
+          }
+        }
       } else {
         const float inv = 1.f / wsum;
 #pragma unroll
@@ -296,8 +378,8 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
 // lanes of a point split the rsqrt of the step s.  The standalone batch kernel measured 3.6%
 // faster with it; the NLEM kernels of one pixel per CTA measured 2-5% slower, so they do not
 // take it (the register allocation decides).
-template <class C, bool SPLIT = false, class X = NoExchange>
-__device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm) {
+template <class C, bool SPLIT = false, class X = NoExchange, class PJ = ScalarBox>
+__device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm, const PJ& pj = PJ()) {
   static_assert(!SPLIT || C::G == 2, "the split rsqrt pairs the two lanes of a point");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
   const bool last = (g == C::G - 1);
@@ -506,60 +588,139 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
         si[6] = (it + 1 == prm.iters || (prm.tol > 0.f && periodic)) ? 1 : 0;
       }
       float p_dd = 0.f, p_dS = 0.f, p_zz = 0.f, p_zx = 0.f, p_dz = 0.f, p_dzA = 0.f, p_E = 0.f, p_G = 0.f;
+      if constexpr (std::is_same<PJ, ScalarBox>::value) {
 #pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        const int col = lane + 32 * h2;
-        if (col >= C::COLS) continue;
-        const float4 tv = h2 == 0 ? t0 : t1;
-        const int sg = col / C::NQR, quad = col - sg * C::NQR;
-        const int real = slice_real<C>(sg, d);
-        // this lane's four slots of z, c and sum g as one 16-byte access each (slots past the
-        // slice's real coordinates stay zero)
-        const bool has_z = quad < C::NQA;
-        const int vi0 = sg * C::QA + 4 * quad;
-        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), c4o = z4, s4o = z4;
-        if (has_z) {
-          z4 = *reinterpret_cast<const float4*>(sm.zv + vi0);
-          if (check) {
-            c4o = *reinterpret_cast<const float4*>(sm.cv + vi0);
-            s4o = *reinterpret_cast<const float4*>(sm.sgv + vi0);
-          }
-        }
-        float zn[4], cn[4], sn[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int slot = 4 * quad + i;
-          const float A = f4get(tv, i);
-          zn[i] = cn[i] = sn[i] = 0.f;
-          if (slot < real) {
-            const float z = f4get(z4, i);
-            const float znew = clampf(fmaf(-A, inv_n, z), prm.lo, prm.hi);
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int col = lane + 32 * h2;
+          if (col >= C::COLS) continue;
+          const float4 tv = h2 == 0 ? t0 : t1;
+          const int sg = col / C::NQR, quad = col - sg * C::NQR;
+          const int real = slice_real<C>(sg, d);
+          // this lane's four slots of z, c and sum g as one 16-byte access each (slots past the
+          // slice's real coordinates stay zero)
+          const bool has_z = quad < C::NQA;
+          const int vi0 = sg * C::QA + 4 * quad;
+          float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), c4o = z4, s4o = z4;
+          if (has_z) {
+            z4 = *reinterpret_cast<const float4*>(sm.zv + vi0);
             if (check) {
-              const float c = f4get(c4o, i);
-              const float sgp = f4get(s4o, i);
-              const float del = c - znew;          // delta = c(t) - z(t+1)
-              const float SD = sgp - A;            // sum_k (g_k(t) - g_k(t+1))
-              const float dz = z - znew;
-              p_dd = fmaf(del, del, p_dd);
-              p_dS = fmaf(del, SD, p_dS);
-              p_zz = fmaf(znew, znew, p_zz);
-              p_zx = fmaf(znew, fmaf(fn, del, SD), p_zx);
-              p_dz = fmaf(dz, dz, p_dz);
-              p_dzA = fmaf(dz, A, p_dzA);
+              c4o = *reinterpret_cast<const float4*>(sm.cv + vi0);
+              s4o = *reinterpret_cast<const float4*>(sm.sgv + vi0);
             }
-            zn[i] = znew;
-            cn[i] = 2.f * znew - z;
-            sn[i] = A;
-          } else if (slot == C::Q) {
-            p_E += A;
-          } else if (slot == C::Q + 1) {
-            p_G += A;
+          }
+          float zn[4], cn[4], sn[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int slot = 4 * quad + i;
+            const float A = f4get(tv, i);
+            zn[i] = cn[i] = sn[i] = 0.f;
+            if (slot < real) {
+              const float z = f4get(z4, i);
+              const float znew = clampf(fmaf(-A, inv_n, z), prm.lo, prm.hi);
+              if (check) {
+                const float c = f4get(c4o, i);
+                const float sgp = f4get(s4o, i);
+                const float del = c - znew;          // delta = c(t) - z(t+1)
+                const float SD = sgp - A;            // sum_k (g_k(t) - g_k(t+1))
+                const float dz = z - znew;
+                p_dd = fmaf(del, del, p_dd);
+                p_dS = fmaf(del, SD, p_dS);
+                p_zz = fmaf(znew, znew, p_zz);
+                p_zx = fmaf(znew, fmaf(fn, del, SD), p_zx);
+                p_dz = fmaf(dz, dz, p_dz);
+                p_dzA = fmaf(dz, A, p_dzA);
+              }
+              zn[i] = znew;
+              cn[i] = 2.f * znew - z;
+              sn[i] = A;
+            } else if (slot == C::Q) {
+              p_E += A;
+            } else if (slot == C::Q + 1) {
+              p_G += A;
+            }
+          }
+          if (has_z) {
+            *reinterpret_cast<float4*>(sm.zv + vi0) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+            *reinterpret_cast<float4*>(sm.cv + vi0) = make_float4(cn[0], cn[1], cn[2], cn[3]);
+            *reinterpret_cast<float4*>(sm.sgv + vi0) = make_float4(sn[0], sn[1], sn[2], sn[3]);
           }
         }
-        if (has_z) {
-          *reinterpret_cast<float4*>(sm.zv + vi0) = make_float4(zn[0], zn[1], zn[2], zn[3]);
-          *reinterpret_cast<float4*>(sm.cv + vi0) = make_float4(cn[0], cn[1], cn[2], cn[3]);
-          *reinterpret_cast<float4*>(sm.sgv + vi0) = make_float4(sn[0], sn[1], sn[2], sn[3]);
+      } else {
+        // any other set: form v = z - sum g / n for the lane's eight values, project them together,
+        // then the same residual terms and stores as above
+        float v[8], zo[8], co[8], so[8], Av[8];
+        int q[8];
+        bool ok[8];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int col = lane + 32 * h2;
+          const bool colok = col < C::COLS;
+          const float4 tv = h2 == 0 ? t0 : t1;
+          const int sg = colok ? col / C::NQR : 0, quad = colok ? col - sg * C::NQR : 0;
+          const int real = slice_real<C>(sg, d);
+          const bool has_z = colok && quad < C::NQA;
+          const int vi0 = sg * C::QA + 4 * quad;
+          float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), c4o = z4, s4o = z4;
+          if (has_z) {
+            z4 = *reinterpret_cast<const float4*>(sm.zv + vi0);
+            if (check) {
+              c4o = *reinterpret_cast<const float4*>(sm.cv + vi0);
+              s4o = *reinterpret_cast<const float4*>(sm.sgv + vi0);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = 4 * h2 + i, slot = 4 * quad + i;
+            const float A = f4get(tv, i);
+            ok[k] = colok && slot < real;
+            q[k] = sg * C::Q + slot;
+            zo[k] = f4get(z4, i);
+            co[k] = f4get(c4o, i);
+            so[k] = f4get(s4o, i);
+            Av[k] = A;
+            v[k] = ok[k] ? fmaf(-A, inv_n, zo[k]) : 0.f;
+            if (colok && !ok[k]) {
+              if (slot == C::Q) p_E += A;
+              else if (slot == C::Q + 1) p_G += A;
+            }
+          }
+        }
+        project_lane(pj, v, q, ok);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int col = lane + 32 * h2;
+          const bool colok = col < C::COLS;
+          const int sg = colok ? col / C::NQR : 0, quad = colok ? col - sg * C::NQR : 0;
+          const bool has_z = colok && quad < C::NQA;
+          float zn[4], cn[4], sn[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = 4 * h2 + i;
+            zn[i] = cn[i] = sn[i] = 0.f;
+            if (ok[k]) {
+              const float znew = v[k], z = zo[k], A = Av[k];
+              if (check) {
+                const float del = co[k] - znew;
+                const float SD = so[k] - A;
+                const float dz = z - znew;
+                p_dd = fmaf(del, del, p_dd);
+                p_dS = fmaf(del, SD, p_dS);
+                p_zz = fmaf(znew, znew, p_zz);
+                p_zx = fmaf(znew, fmaf(fn, del, SD), p_zx);
+                p_dz = fmaf(dz, dz, p_dz);
+                p_dzA = fmaf(dz, A, p_dzA);
+              }
+              zn[i] = znew;
+              cn[i] = 2.f * znew - z;
+              sn[i] = A;
+            }
+          }
+          if (has_z) {
+            const int vi0 = sg * C::QA + 4 * quad;
+            *reinterpret_cast<float4*>(sm.zv + vi0) = make_float4(zn[0], zn[1], zn[2], zn[3]);
+            *reinterpret_cast<float4*>(sm.cv + vi0) = make_float4(cn[0], cn[1], cn[2], cn[3]);
+            *reinterpret_cast<float4*>(sm.sgv + vi0) = make_float4(sn[0], sn[1], sn[2], sn[3]);
+          }
         }
       }
       if (check) {

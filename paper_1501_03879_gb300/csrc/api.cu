@@ -205,6 +205,56 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
   return NLEM_OK;
 }
 
+int em_solve_batch_set(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n, int d,
+                       const nlem_set* set, float rho, int iters, const float* x0, const nlem_options* opt,
+                       float* x_out, int* iters_used, float* residual, void* stream) {
+  const nlem_box any = {0.f, 0.f};
+  int rc = check_common(ctx, any, rho, iters, opt);
+  if (rc) return rc;
+  if ((rc = admm_only(opt, "em_solve_batch_set"))) return rc;
+  if (!set) return fail(NLEM_ERR_INVALID, "set is NULL");
+  if (set->kind == NLEM_SET_COORD_BOXES) {
+    if (!set->lo || !set->hi) return fail(NLEM_ERR_INVALID, "coordinate boxes need lo and hi");
+  } else if (set->kind == NLEM_SET_BALL) {
+    if (!set->center) return fail(NLEM_ERR_INVALID, "the ball needs its centre");
+    if (!(set->radius >= 0.f) || !finite(set->radius))
+      return fail(NLEM_ERR_INVALID, "radius must be finite and >= 0 (got %g)", set->radius);
+  } else {
+    return fail(NLEM_ERR_INVALID, "unknown set kind %d", set->kind);
+  }
+  if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
+  if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
+  if (d < 1 || d > 148) return fail(NLEM_ERR_INVALID, "d must be in [1, 148] (got %d)", d);
+  if (B == 0) return NLEM_OK;
+  if (!points || !weights || !x_out) return fail(NLEM_ERR_INVALID, "points, weights and x_out must be non-NULL");
+  if (n > nlemk::em_set_capacity(d))
+    return fail(NLEM_ERR_UNSUPPORTED, "n = %d exceeds the %d points the set kernels hold for d = %d", n,
+                nlemk::em_set_capacity(d), d);
+  if (opt && opt->fp64_check)
+    return fail(NLEM_ERR_UNSUPPORTED, "the FP64 check is the box's; not available for other sets");
+  if ((rc = set_device(ctx))) return rc;
+  nlemk::EmLaunch L;
+  L.pts = points;
+  L.w = weights;
+  L.B = B;
+  L.n = n;
+  L.d = d;
+  L.prm = make_params(any, rho, iters, opt, d);
+  L.x0 = x0;
+  L.x_out = x_out;
+  L.iters_used = iters_used;
+  L.resid = residual;
+  L.obj64 = nullptr;
+  L.kkt64 = nullptr;
+  L.sm_count = ctx->sm_count;
+  L.stream = (cudaStream_t)stream;
+  const float* a = set->kind == NLEM_SET_BALL ? set->center : set->lo;
+  const int e = nlemk::launch_em_set(L, set->kind, a, set->hi, set->radius);
+  if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for n = %d, d = %d", n, d);
+  if (e != 0) return cuda_fail((cudaError_t)e, "em_solve_batch_set launch");
+  return NLEM_OK;
+}
+
 int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, int d, nlem_box box, float rho,
              int iters, float* x_out, void* stream) {
   return em_solve_batch(ctx, points, weights, 1, n, d, box, rho, iters, nullptr, nullptr, x_out, nullptr, nullptr,

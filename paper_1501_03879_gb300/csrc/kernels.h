@@ -88,6 +88,10 @@ bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
+// Standalone batch over per-coordinate boxes (kind 1: a = lo, b = hi, device [d]) or the ball
+// ||x - a|| <= r (kind 2: a = centre, device [d]); its point capacity for dimension d.
+int launch_em_set(const EmLaunch& L, int kind, const float* a, const float* b, float r);
+int em_set_capacity(int d);
 // Multichannel NLEM (3 channels; patch 5 or 7): the largest window point count, or 0; and the
 // largest one CTA holds (larger windows split each pixel over a two-CTA cluster).
 int nlem_color_capacity(int channels, int patch);

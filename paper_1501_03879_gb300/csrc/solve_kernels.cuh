@@ -14,12 +14,14 @@ namespace nlemk {
 // standalone batch: points [B][n][d] and weights [B][n] streamed from HBM into the CTA's
 // shared-memory point rows, one problem per CTA iteration
 // ------------------------------------------------------------------------------------------
-template <class C>
+// PJ: the constraint set (ScalarBox = the box of SolveParams; CoordBoxes, Ball from admm_core.cuh).
+template <class C, class PJ = ScalarBox>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, long long B, int n,
                 int d, SolveParams prm, const float* __restrict__ x0, float* __restrict__ x_out,
                 int* __restrict__ iters_used, float* __restrict__ resid, double* __restrict__ obj64,
-                double* __restrict__ kkt64) {
+                double* __restrict__ kkt64, PJ pj = PJ()) {
+  constexpr bool kBox = std::is_same<PJ, ScalarBox>::value;
   extern __shared__ float4 smem_raw[];
   Smem<C> sm(reinterpret_cast<float*>(smem_raw));
   const int t = threadIdx.x;
@@ -67,12 +69,19 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       for (int i = t; i < C::VEC; i += C::NT) {
         const int sg = i / C::QA, slot = i - sg * C::QA;
         const int real = slice_real<C>(sg, dd);
-        const float z = slot < real ? clampf(__ldg(x0 + (size_t)b * dd + sg * C::Q + slot), prm.lo, prm.hi) : 0.f;
+        const float xv = slot < real ? __ldg(x0 + (size_t)b * dd + sg * C::Q + slot) : 0.f;
+        const float z = kBox ? clampf(xv, prm.lo, prm.hi) : xv;
         sm.zv[i] = z;
         sm.cv[i] = z;
         sm.sgv[i] = 0.f;
       }
       __syncthreads();
+      if constexpr (!kBox) {   // any other set: warp 0 projects the whole start vector
+        if (t < 32) project_zv<C>(sm, dd, pj);
+        __syncthreads();
+        for (int i = t; i < C::VEC; i += C::NT) sm.cv[i] = sm.zv[i];
+        __syncthreads();
+      }
     } else {
       float wreg[C::P];
       const int pg = lane_group<C>();
@@ -81,9 +90,9 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
         const int j = pg + p * C::NG;
         wreg[p] = j < n ? __ldg(Wt + j) : 0.f;
       }
-      weighted_mean_start<C>(sm, wreg, n, dd, prm);
+      weighted_mean_start<C, NoExchange, PJ>(sm, wreg, n, dd, prm, pj);
     }
-    admm_iterate<C, C::G == 2>(sm, n, dd, prm);
+    admm_iterate<C, C::G == 2, NoExchange, PJ>(sm, n, dd, prm, pj);
     for (int q = t; q < dd; q += C::NT) {
       const int sg = q / C::Q, i = q - sg * C::Q;
       x_out[(size_t)b * dd + q] = sm.zv[sg * C::QA + i];
@@ -92,7 +101,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       if (iters_used) iters_used[b] = (int)sm.scal[2];
       if (resid) resid[b] = sm.scal[3];
     }
-    if (obj64 || kkt64) {
+    if (kBox && (obj64 || kkt64)) {   // the projected-gradient residual is the box's
       double F, R;
       fp64_check<C>(sm, n, dd, prm, [&](int j) { return (double)__ldg(Wt + j); }, F, R);
       if (t == 0) {
@@ -292,9 +301,9 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <class C>
-inline int launch_em(const EmLaunch& L, int grid_mult) {
-  auto kern = em_batch_kernel<C>;
+template <class C, class PJ = ScalarBox>
+inline int launch_em(const EmLaunch& L, int grid_mult, const PJ& pj = PJ()) {
+  auto kern = em_batch_kernel<C, PJ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
   if (e != cudaSuccess) return (int)e;
   long long grid = L.B;
@@ -302,7 +311,7 @@ inline int launch_em(const EmLaunch& L, int grid_mult) {
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.pts, L.w, L.B, L.n, L.d, L.prm, L.x0, L.x_out,
-                                                          L.iters_used, L.resid, L.obj64, L.kkt64);
+                                                          L.iters_used, L.resid, L.obj64, L.kkt64, pj);
   return (int)cudaGetLastError();
 }
 

@@ -358,3 +358,82 @@ def test_tolerance_stopping_rule():
     # fixed count: same iterate as tol-mode at that count
     zf, usedf, _, _ = oracle.em_admm(pts, w, 0.0, 255.0, 0.01, used)
     assert usedf == used and np.array_equal(zf, z)
+
+
+# ---------------------------------------------------------------------------------------
+# constraint sets beyond the box (Sec. 2 needs only a closed convex C with a simple projection)
+# ---------------------------------------------------------------------------------------
+
+def test_project_set_ball_and_boxes():
+    rng = np.random.default_rng(40)
+    c = np.array([3.0, -1.0])
+    r = 2.5
+    gx, gy = np.meshgrid(np.linspace(c[0] - r, c[0] + r, 801), np.linspace(c[1] - r, c[1] + r, 801))
+    grid = np.stack([gx.ravel(), gy.ravel()], 1)
+    grid = grid[np.sum((grid - c) ** 2, 1) <= r * r]
+    for _ in range(20):
+        x = rng.uniform(-6, 10, 2)
+        p = oracle.project_set(x, oracle.SET_BALL, c, r=r)
+        dmin = np.sqrt(np.min(np.sum((grid - x) ** 2, 1)))           # brute-force distance to the ball
+        assert np.linalg.norm(p - c) <= r + 1e-12
+        assert dmin - 2 * (2 * r / 800) <= np.linalg.norm(x - p) <= dmin + 1e-12
+        assert np.allclose(oracle.project_set(p, oracle.SET_BALL, c, r=r), p, atol=1e-12)
+    inside = c + np.array([0.3, -0.7])
+    assert np.array_equal(oracle.project_set(inside, oracle.SET_BALL, c, r=r), inside)
+    assert np.array_equal(oracle.project_set(np.array([5.0, 1.0]), oracle.SET_BALL, c, r=0.0), c)
+    lo, hi = np.array([0.0, -2.0, 5.0]), np.array([1.0, 2.0, 5.0])
+    x = np.array([-3.0, 0.5, 9.0])
+    assert np.array_equal(oracle.project_set(x, oracle.SET_COORD_BOXES, lo, hi), np.array([0.0, 0.5, 5.0]))
+
+
+def test_em_admm_set_reduces_to_known_cases():
+    rng = np.random.default_rng(41)
+    pts = rng.uniform(0, 255, (25, 4))
+    w = rng.uniform(0.2, 1, 25)
+    # equal per-coordinate bounds are the scalar box: the same iterates as em_admm
+    za, ua, rpa, rda = oracle.em_admm(pts, w, 20.0, 200.0, 0.5, 60, tol=1e-6, check_every=3)
+    zb, ub, rpb, rdb = oracle.em_admm_set(pts, w, oracle.SET_COORD_BOXES, np.full(4, 20.0), np.full(4, 200.0),
+                                          mu=0.5, iters=60, tol=1e-6, check_every=3)
+    assert np.array_equal(za, zb) and ua == ub and rpa == rpb and rda == rdb
+    # a ball that holds every point changes nothing; radius 0 pins the centre
+    zu, *_ = oracle.em_admm(pts, w, -1e9, 1e9, 0.5, 400)
+    zl, *_ = oracle.em_admm_set(pts, w, oracle.SET_BALL, pts.mean(0), r=1e6, mu=0.5, iters=400)
+    assert np.allclose(zl, zu, atol=1e-9)
+    c = np.array([1.0, 2.0, 3.0, 4.0])
+    z0, *_ = oracle.em_admm_set(pts, w, oracle.SET_BALL, c, r=0.0, mu=0.5, iters=30)
+    assert np.allclose(z0, c, atol=1e-12)
+    # d = 1 boxes: the weighted median clamped to [lo, hi]
+    v = rng.uniform(0, 10, 9)
+    wv = rng.uniform(0.1, 1, 9)
+    order = np.argsort(v)
+    cum = np.cumsum(wv[order])
+    med = v[order][np.searchsorted(cum, 0.5 * cum[-1])]
+    for lo, hi in ((0.0, 10.0), (med + 0.5, 12.0), (-1.0, med - 0.7)):
+        z, *_ = oracle.em_admm_set(v[:, None], wv, oracle.SET_COORD_BOXES, np.array([lo]), np.array([hi]), mu=0.05,
+                                   iters=4000)
+        F = lambda t: float(np.sum(wv * np.abs(t - v)))
+        assert F(z[0]) <= F(min(max(med, lo), hi)) * (1 + 1e-7) + 1e-9
+        assert lo - 1e-12 <= z[0] <= hi + 1e-12
+
+
+def test_em_admm_set_two_dimensional_brute_force():
+    """d = 2: the converged objective is the minimum over a fine grid of the set, up to the grid's
+    Lipschitz bound (sum w times half a grid diagonal)."""
+    rng = np.random.default_rng(42)
+    pts = rng.uniform(0, 10, (12, 2))
+    w = rng.uniform(0.2, 1, 12)
+    F = lambda Z: np.sum(w[None, :] * np.linalg.norm(Z[:, None, :] - pts[None, :, :], axis=2), axis=1)
+    c, r = np.array([1.0, 1.0]), 2.0                                  # a ball away from the points
+    z, *_ = oracle.em_admm_set(pts, w, oracle.SET_BALL, c, r=r, mu=0.1, iters=6000)
+    gx, gy = np.meshgrid(np.linspace(-1, 3, 401), np.linspace(-1, 3, 401))
+    grid = np.stack([gx.ravel(), gy.ravel()], 1)
+    grid = grid[np.sum((grid - c) ** 2, 1) <= r * r]
+    step = 4.0 / 400
+    assert np.linalg.norm(z - c) <= r + 1e-9
+    assert F(z[None])[0] <= F(grid).min() + w.sum() * step + 1e-9
+    lo, hi = np.array([6.0, 0.0]), np.array([9.0, 2.0])                # a box on one side of the points
+    z, *_ = oracle.em_admm_set(pts, w, oracle.SET_COORD_BOXES, lo, hi, mu=0.1, iters=6000)
+    gx, gy = np.meshgrid(np.linspace(6, 9, 301), np.linspace(0, 2, 201))
+    grid = np.stack([gx.ravel(), gy.ravel()], 1)
+    assert np.all(z >= lo - 1e-12) and np.all(z <= hi + 1e-12)
+    assert F(z[None])[0] <= F(grid).min() + w.sum() * 0.01 + 1e-9
