@@ -109,8 +109,8 @@ PROFILED = {
                          "issue_pct": 46.53, "smem_wavefront_pct": 42.13},
     "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
                     "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "45234b161c959ca3", "traffic": (361691136 + 3998464) * 64, "fma_pipe_pct": 41.57,
-                        "issue_pct": 35.44, "smem_wavefront_pct": 66.81},
+    "em_batch_kernel": {"sources": "bd61b46b57b4306d", "traffic": (361708800 + 4032768) * 64, "fma_pipe_pct": 41.57,
+                        "issue_pct": 35.43, "smem_wavefront_pct": 66.74},
 }
 
 
@@ -582,13 +582,13 @@ def extra_color(nl, ctx):
 
 
 def extra_sets(nl, ctx):
-    """Standalone batches over constraint sets beyond the box: 16384 problems of 256 points in
-    d = 49 (the set kernels' runtime-dimension shape), per-coordinate boxes and a ball that cuts
-    the solutions, rho = 1, 60 iterations; solves/s and the solver's FP32 rate."""
+    """Standalone batches over constraint sets beyond the box: 16384 problems of 441 points in
+    d = 49, per-coordinate boxes and a ball that cuts the solutions, rho = 1, 60 iterations, against
+    the box on the same problems; solves/s and the solver's FP32 rate."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
-    B, n, d, T = 16384, 256, EM_D, 60
+    B, n, d, T = 16384, EM_N, EM_D, 60
     pts = torch.empty((B, n, d), device=dev)
     if not os.path.exists(synth.SYNTH_LIB):
         synth.build_device_generator()
@@ -603,7 +603,7 @@ def extra_sets(nl, ctx):
         fl = em_flops(np.full(B, T), n, d)
         rows.append({"set": name, "solves_per_s": B / (ms * 1e-3), "tflops": fl / (ms * 1e-3) / 1e12, "ms": ms})
     ms, _ = _timed(lambda: nl.em_solve_batch(pts, w, rho=1.0, iters=T, ctx=ctx), reps=3)
-    rows.append({"set": "box (em_solve_batch, d = 49 shape)", "solves_per_s": B / (ms * 1e-3),
+    rows.append({"set": "box (em_solve_batch)", "solves_per_s": B / (ms * 1e-3),
                  "tflops": em_flops(np.full(B, T), n, d) / (ms * 1e-3) / 1e12, "ms": ms})
     del pts
     return {"workload": f"{B} problems, n={n}, d={d}, rho=1, {T} iterations", "rows": rows}

@@ -137,7 +137,7 @@ typedef struct {
  * (x0, or the weighted mean) are projected onto the set instead of the box.  The coordinate
  * boxes clamp each coordinate; the ball pulls a point outside it radially onto the sphere.
  *   points, weights, x0, x_out, iters_used, residual: as em_solve_batch.
- * Runs on the runtime-dimension kernels: d <= 148, n at most 512 (d <= 28) or 256 (d <= 148).
+ * Runs on the box kernels' shapes: d <= 148, n at most 896 (d = 49), 512 (other d <= 28) or 256.
  * Errors: as em_solve_batch; -1 also for a NULL set, an unknown kind, NULL set arrays, a radius
  * that is negative or not finite, or the IRLS solver; -5 for n above the capacity or the FP64
  * check (its optimality residual is the box's).  B == 0 returns 0 at once.

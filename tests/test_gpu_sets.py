@@ -34,7 +34,8 @@ def _t(a):
 
 
 # every runtime-dimension shape (d <= 28, 60, 120, 148), sizes up to each one's capacity
-@pytest.mark.parametrize("n,d", [(500, 9), (441, 25), (256, 49), (200, 100), (256, 147), (33, 2)])
+@pytest.mark.parametrize("n,d", [(500, 9), (441, 25), (256, 49), (441, 49), (800, 49), (200, 100), (256, 147),
+                                 (33, 2)])
 def test_coordinate_boxes_against_oracle(nl, n, d):
     B = 12
     pts = synth.em_points(7100 + d, np.arange(B), n, d)
@@ -51,7 +52,8 @@ def test_coordinate_boxes_against_oracle(nl, n, d):
     assert np.all(r["iters_used"].cpu().numpy() == 50)
 
 
-@pytest.mark.parametrize("n,d,radius", [(256, 49, 40.0), (256, 147, 150.0), (100, 5, 0.0), (250, 60, 1e4)])
+@pytest.mark.parametrize("n,d,radius", [(256, 49, 40.0), (441, 49, 40.0), (256, 147, 150.0), (100, 5, 0.0),
+                                        (250, 60, 1e4)])
 def test_ball_against_oracle(nl, n, d, radius):
     """A ball centred away from the points (the solution on its sphere), a zero radius (the centre)
     and a radius holding every point (the unconstrained median)."""
@@ -114,7 +116,7 @@ def test_sets_argument_errors(nl):
     with pytest.raises(nl.NlemError) as e:
         nl.em_solve_batch_set(pts, w, center=c, radius=float("inf"))
     assert e.value.code == -1
-    with pytest.raises(nl.NlemError) as e:          # above the 256 points of the d <= 148 shapes
+    with pytest.raises(nl.NlemError) as e:          # above the 256 points of the d = 29..148 shapes
         nl.em_solve_batch_set(torch.zeros((1, 300, 40), device=DEV), torch.ones((1, 300), device=DEV),
                               center=torch.zeros(40, device=DEV), radius=1.0)
     assert e.value.code == -5
