@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--profile-case", choices=["traffic", "bf16", "features", "irls"], default=None,
+    p.add_argument("--profile-case", choices=["traffic", "bf16", "features", "irls", "color", "sets"], default=None,
                    help="run a small profiling case (no timing output) and exit")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra rows (rho=1e-3, mixed precision, batch, learned warm start)")
@@ -144,7 +144,9 @@ def profile_case(which="traffic"):
     per-problem settings.  bf16: the tensor-core weight table of a 256x256 image (sigma 30 + 5%
     impulses, 9x9 patches, 21x21 window).  features: the warm-start features of a 256x256 image
     (7x7 patches, 21x21 window).  irls: NLEM-IRLS, 40 steps from the noisy patch, on a 128x128
-    image (sigma 20, h = 200, 7x7 patches, 21x21 window)."""
+    image (sigma 20, h = 200, 7x7 patches, 21x21 window).  color: 7x7 colour patches at the 21x21
+    window (two-CTA clusters) on a 128x128x3 image, 20 iterations.  sets: 4096 standalone problems
+    of 441 x 49 in a ball of radius 200, rho = 1, 60 iterations."""
     import torch
     import synth
     import paper_1501_03879_gb300 as nl
@@ -157,6 +159,25 @@ def profile_case(which="traffic"):
                 nl.nlem_bf16_weights(gi, 9, 21, 300.0)
             else:
                 nl.nlem_features(gi, 7, 21, 250.0)
+        torch.cuda.synchronize()
+        return
+    if which == "color":
+        g = np.stack([synth.noisy_image(10013 + c, 128, 128, 20.0)[0] for c in range(3)])
+        gi = torch.from_numpy(g).to(dev)
+        for _ in range(2):
+            nl.nlem_denoise_color(gi, patch=7, window=S_WIN, h=200.0 * math.sqrt(3.0), rho=RHO, iters=20)
+        torch.cuda.synchronize()
+        return
+    if which == "sets":
+        B = 4096
+        pts = torch.empty((B, EM_N, EM_D), device=dev)
+        if not os.path.exists(synth.SYNTH_LIB):
+            synth.build_device_generator()
+        synth.device_em_points(SEED, B, EM_N, EM_D, pts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        w = torch.from_numpy(synth.em_weights(SEED, np.arange(B), EM_N)).to(dev)
+        c = torch.full((EM_D,), 60.0, device=dev)
+        for _ in range(2):
+            nl.em_solve_batch_set(pts, w, center=c, radius=200.0, rho=RHO, iters=60)
         torch.cuda.synchronize()
         return
     if which == "irls":
