@@ -12,6 +12,9 @@
  *   conjugate prox          Sec. 2, Eqs. (CF), (proxfstar): projection onto the lam-ball
  *   EM-ADMM                 Sec. 2, Algorithm 1 with Eqs. (updatex), (updatez), (updatey)
  *   box projection          Sec. 3, coordinate-wise clamp to [l, u]
+ *   accelerated EM-ADMM     Sec. 4 names accelerated ADMM as future work; orc_em_admm_fast
+ *                           follows Goldstein, O'Donoghue, Setzer and Baraniuk (2014), fast ADMM
+ *                           with restart for problems that are not strongly convex
  *   NLEM                    Sec. 3, Eq. (L1regression): patches, weights exp(-||Pi-Pj||^2/h^2),
  *                           window S(i), centre pixel of the denoised patch
  *
@@ -169,6 +172,110 @@ void orc_weighted_mean_start(const double *pts, const double *w, int n, int d, d
  * The residuals of the last iteration run are always returned (0 if iters == 0).
  * Returns 0, or -1 if memory runs out.
  * ------------------------------------------------------------------------------------- */
+/* Algorithm 1 with Nesterov-type momentum and restart (fast ADMM with restart; Goldstein et al.
+ * 2014, the variant for objectives that are not strongly convex).  Steps (x, z, y) are those of
+ * Algorithm 1, taken at the extrapolated z_hat and y_hat.  After each step the combined residual
+ * c = ||y - y_hat||^2 / mu + mu * n * ||z - z_hat||^2 decides: if c < eta * c_prev the momentum
+ * grows, alpha+ = (1 + sqrt(1 + 4 alpha^2)) / 2, and z_hat, y_hat step beyond the new iterate by
+ * (alpha - 1) / alpha+ times its change; otherwise alpha = 1, z_hat and y_hat restart from the
+ * previous iterate and c_prev is divided by eta.  With alpha = 1 at the start, the first two
+ * iterations equal Algorithm 1's.  The stopping rule and residuals are those of orc_em_admm,
+ * evaluated at the step's x, y and z, with z_prev the previous iterate.  *restarts (if not NULL)
+ * counts the restarts. */
+int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo, double hi, double mu,
+                     int iters, const double *z0, double tol, int check_every, double eta, double *z,
+                     int *iters_used, double *rpri, double *rdual, int *restarts) {
+  const size_t nd = (size_t)n * d;
+  double *x = (double *)malloc(sizeof(double) * nd);
+  double *y = (double *)calloc(nd, sizeof(double));
+  double *yh = (double *)calloc(nd, sizeof(double));
+  double *yo = (double *)calloc(nd, sizeof(double));
+  double *r = (double *)malloc(sizeof(double) * (size_t)d);
+  double *v = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zh = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zo = (double *)malloc(sizeof(double) * (size_t)d);
+  if (!x || !y || !yh || !yo || !r || !v || !zh || !zo) {
+    free(x); free(y); free(yh); free(yo); free(r); free(v); free(zh); free(zo);
+    return -1;
+  }
+  if (z0) {
+    for (int q = 0; q < d; ++q) z[q] = z0[q];
+  } else {
+    orc_weighted_mean_start(pts, w, n, d, lo, hi, z);
+  }
+  for (int q = 0; q < d; ++q) zh[q] = zo[q] = z[q];
+  if (check_every < 1) check_every = 1;
+  double alpha = 1.0, c_prev = INFINITY, rp = 0.0, rd = 0.0;
+  int t_done = 0, nrest = 0;
+  for (int t = 1; t <= iters; ++t) {
+    /* Algorithm 1's step at (z_hat, y_hat) */
+    for (int q = 0; q < d; ++q) r[q] = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double *xk = x + (size_t)k * d;
+      const double *yk = yh + (size_t)k * d;
+      for (int q = 0; q < d; ++q) v[q] = zh[q] - yk[q] / mu;
+      orc_prox(v, pts + (size_t)k * d, w[k] / mu, d, xk);
+      for (int q = 0; q < d; ++q) r[q] += xk[q] + yk[q] / mu;
+    }
+    for (int q = 0; q < d; ++q) z[q] = r[q] / (double)n;
+    orc_project_box(z, d, lo, hi, z);
+    double cy = 0.0, cz = 0.0;
+    for (size_t i = 0; i < nd; ++i) {
+      y[i] = yh[i] + mu * (x[i] - z[i % (size_t)d]);
+      cy += (y[i] - yh[i]) * (y[i] - yh[i]);
+    }
+    for (int q = 0; q < d; ++q) cz += (z[q] - zh[q]) * (z[q] - zh[q]);
+    t_done = t;
+    /* the stopping rule of orc_em_admm at this step's iterate */
+    int check = (t == iters) || (tol > 0.0 && (t % check_every) == 0);
+    if (check) {
+      double spr = 0.0, sx = 0.0, su = 0.0, zz = 0.0, dz = 0.0;
+      for (size_t i = 0; i < nd; ++i) {
+        double e = x[i] - z[i % (size_t)d], u = y[i] / mu;
+        spr += e * e;
+        sx += x[i] * x[i];
+        su += u * u;
+      }
+      for (int q = 0; q < d; ++q) {
+        zz += z[q] * z[q];
+        dz += (z[q] - zo[q]) * (z[q] - zo[q]);
+      }
+      double den_p = sqrt(sx), nzn = sqrt((double)n) * sqrt(zz);
+      if (nzn > den_p) den_p = nzn;
+      if (den_p < 1e-30) den_p = 1e-30;
+      double den_d = sqrt(su);
+      if (den_d < 1e-30) den_d = 1e-30;
+      rp = sqrt(spr) / den_p;
+      rd = sqrt((double)n) * sqrt(dz) / den_d;
+      if (tol > 0.0 && rp < tol && rd < tol) break;
+    }
+    /* momentum or restart */
+    const double c = cy / mu + mu * (double)n * cz;
+    if (c < eta * c_prev) {
+      const double a1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * alpha * alpha));
+      const double beta = (alpha - 1.0) / a1;
+      for (int q = 0; q < d; ++q) zh[q] = z[q] + beta * (z[q] - zo[q]);
+      for (size_t i = 0; i < nd; ++i) yh[i] = y[i] + beta * (y[i] - yo[i]);
+      alpha = a1;
+      c_prev = c;
+    } else {
+      alpha = 1.0;
+      for (int q = 0; q < d; ++q) zh[q] = zo[q];
+      for (size_t i = 0; i < nd; ++i) yh[i] = yo[i];
+      c_prev = c_prev / eta;
+      ++nrest;
+    }
+    for (int q = 0; q < d; ++q) zo[q] = z[q];
+    for (size_t i = 0; i < nd; ++i) yo[i] = y[i];
+  }
+  if (iters_used) *iters_used = t_done;
+  if (rpri) *rpri = rp;
+  if (rdual) *rdual = rd;
+  if (restarts) *restarts = nrest;
+  free(x); free(y); free(yh); free(yo); free(r); free(v); free(zh); free(zo);
+  return 0;
+}
+
 /* Constraint sets other than the box of Sec. 3 (the method needs only a closed convex C with a
  * simple projection, Sec. 2).  kind 1: per-coordinate boxes prod_q [pa[q], pb[q]], projected by
  * clamping each coordinate; kind 2: the ball ||x - pa|| <= r, projected by pulling x radially

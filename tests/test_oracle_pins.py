@@ -8,6 +8,7 @@ import pytest
 from scipy.optimize import minimize, minimize_scalar
 
 import oracle
+import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -437,3 +438,60 @@ def test_em_admm_set_two_dimensional_brute_force():
     grid = np.stack([gx.ravel(), gy.ravel()], 1)
     assert np.all(z >= lo - 1e-12) and np.all(z <= hi + 1e-12)
     assert F(z[None])[0] <= F(grid).min() + w.sum() * 0.01 + 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# accelerated Algorithm 1 (fast ADMM with restart; Sec. 4 names accelerated ADMM as future work)
+# ---------------------------------------------------------------------------------------
+
+def test_fast_admm_starts_as_algorithm_1():
+    """alpha starts at 1, so the first extrapolation has weight 0: iterations 1 and 2 are
+    Algorithm 1's, bit for bit; the third differs."""
+    rng = np.random.default_rng(50)
+    pts = rng.uniform(0, 255, (30, 5))
+    w = rng.uniform(0.1, 1, 30)
+    for T in (1, 2):
+        za, *_ = oracle.em_admm(pts, w, 0.0, 255.0, 0.3, T)
+        zf, *_ = oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.3, T)
+        assert np.array_equal(za, zf)
+    za, *_ = oracle.em_admm(pts, w, 0.0, 255.0, 0.3, 3)
+    zf, *_ = oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.3, 3)
+    assert not np.array_equal(za, zf)
+
+
+def test_fast_admm_converges_to_the_optimum():
+    rng = np.random.default_rng(51)
+    for trial in range(4):
+        pts = rng.uniform(0, 255, (25, 6))
+        w = rng.uniform(0.1, 1, 25)
+        z_ref = _converged(pts, w, 20.0, 230.0, mu=0.05, iters=20000)
+        zf, used, *_ = oracle.em_admm_fast(pts, w, 20.0, 230.0, 0.05, 20000, tol=1e-12, check_every=10)
+        F_ref, F_f = oracle.objective(z_ref, pts, w), oracle.objective(zf, pts, w)
+        assert F_f <= F_ref * (1 + 1e-9)
+    # d = 1: the weighted median
+    v = rng.uniform(0, 10, 11)
+    wv = rng.uniform(0.1, 1, 11)
+    order = np.argsort(v)
+    cum = np.cumsum(wv[order])
+    med = v[order][np.searchsorted(cum, 0.5 * cum[-1])]
+    z, *_ = oracle.em_admm_fast(v[:, None], wv, -1e6, 1e6, 0.05, 5000)
+    F = lambda t: float(np.sum(wv * np.abs(t - v)))
+    assert F(z[0]) <= F(med) * (1 + 1e-9) + 1e-12
+    # planar Fermat point of a triangle with all angles below 120 degrees, embedded in R^3
+    A = np.array([[0.0, 0.0, 5.0], [4.0, 0.0, 5.0], [1.0, 3.0, 5.0]])
+    z, *_ = oracle.em_admm_fast(A, np.ones(3), -1e6, 1e6, 0.5, 5000)
+    u = (A - z) / np.linalg.norm(A - z, axis=1)[:, None]
+    assert np.linalg.norm(u.sum(0)) <= 1e-6                 # unit vectors to the vertices sum to zero
+
+
+def test_fast_admm_needs_fewer_iterations_at_large_mu():
+    """On NLEM problems of a synthetic image at mu = 1 (the stopping rule at 1e-4, checked every 10
+    iterations, cap 300) the accelerated variant stops sooner on average than Algorithm 1."""
+    g, _ = synth.noisy_image(9001, 64, 64, 20.0)
+    rng = np.random.default_rng(52)
+    plain, fast = [], []
+    for lin in rng.choice(64 * 64, 16, replace=False):
+        pts, w, _ = oracle.nlem_problem(g, 7, 21, 200.0, int(lin))
+        plain.append(oracle.em_admm(pts, w, 0.0, 255.0, 1.0, 300, tol=1e-4, check_every=10)[1])
+        fast.append(oracle.em_admm_fast(pts, w, 0.0, 255.0, 1.0, 300, tol=1e-4, check_every=10)[1])
+    assert np.mean(fast) < 0.75 * np.mean(plain), (np.mean(fast), np.mean(plain))
