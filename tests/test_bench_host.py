@@ -58,3 +58,19 @@ def test_source_hash_ignores_comments_and_whitespace():
     assert b._code_only("int a; // note\n  /* block\n comment */ float b;\n\n") == "int a; float b;"
     assert b._code_only("x = 1; // one") == b._code_only("x =\t1;\n")
     assert b._code_only("x = 1;") != b._code_only("x = 2;")
+
+
+def test_irls_flop_count_follows_the_stated_convention():
+    b = _bench()
+    n = np.array([[441.0, 121.0]])
+    d = 49
+    want = sum((5 * nn * d + 4 * nn) * 4 + 5 * nn * d + 3 * nn for nn in (441, 121))
+    assert b.irls_flops(n, 4, d) == want
+
+
+def test_profile_cases_are_the_documented_ones():
+    b = _bench()
+    import inspect
+    doc = inspect.getdoc(b.profile_case)
+    for case in ("traffic", "bf16", "features", "irls", "color", "sets"):
+        assert f"{case}:" in doc
