@@ -495,3 +495,94 @@ def test_fast_admm_needs_fewer_iterations_at_large_mu():
         plain.append(oracle.em_admm(pts, w, 0.0, 255.0, 1.0, 300, tol=1e-4, check_every=10)[1])
         fast.append(oracle.em_admm_fast(pts, w, 0.0, 255.0, 1.0, 300, tol=1e-4, check_every=10)[1])
     assert np.mean(fast) < 0.75 * np.mean(plain), (np.mean(fast), np.mean(plain))
+
+
+# ---------------------------------------------------------------------------------------
+# the optimality residual at points that are NOT optimal (reading C7), worked by hand
+# ---------------------------------------------------------------------------------------
+
+def test_kkt_residual_interior_point_by_hand():
+    # z = 0, a_1 = (3, 0), a_2 = (0, 4), a_3 = (-5, 0), w = (1, 1, 3): the unit vectors
+    # (z - a_k)/||z - a_k|| are (-1, 0), (0, -1), (1, 0), so g = (2, -1) and sum w = 5.
+    # z - g / sum w = (-0.4, 0.2); inside the box nothing clamps and R = sqrt(0.2).
+    z = np.zeros(2)
+    pts = np.array([[3.0, 0.0], [0.0, 4.0], [-5.0, 0.0]])
+    w = np.array([1.0, 1.0, 3.0])
+    assert oracle.kkt_residual(z, pts, w, -10.0, 10.0) == pytest.approx(math.sqrt(0.2), rel=1e-14)
+    # dropping the division by sum w would give ||g|| = sqrt(5); the scale is fixed by the
+    # gradient of problem (1): its central finite difference has the same norm as g here
+    h = 1e-6
+    grad = np.array([(oracle.objective(z + h * e, pts, w) - oracle.objective(z - h * e, pts, w)) / (2 * h)
+                     for e in np.eye(2)])
+    assert np.allclose(grad, [2.0, -1.0], atol=1e-8)
+    assert oracle.kkt_residual(z, pts, w, -10.0, 10.0) == pytest.approx(np.linalg.norm(grad) / 5.0, rel=1e-7)
+
+
+def test_kkt_residual_with_active_bound_by_hand():
+    # the same points with z on the lower face of C = [0, 10]^2: z - g / sum w = (-0.4, 0.2)
+    # clamps to (0, 0.2), so R = 0.2.  A flipped sign of g would step to (0.4, -0.2), clamp to
+    # (0.4, 0) and give 0.4; the lower bound only blocks the descent direction -g.
+    z = np.zeros(2)
+    pts = np.array([[3.0, 0.0], [0.0, 4.0], [-5.0, 0.0]])
+    w = np.array([1.0, 1.0, 3.0])
+    assert oracle.kkt_residual(z, pts, w, 0.0, 10.0) == pytest.approx(0.2, rel=1e-14)
+    # on the upper face C = [-10, 0]^2 the step clamps to (-0.4, 0): R = 0.4
+    assert oracle.kkt_residual(z, pts, w, -10.0, 0.0) == pytest.approx(0.4, rel=1e-14)
+    # d = 1: points -2, -1, 5 with unit weights give g = 1 + 1 - 1 = 1 at z = 0, so the step
+    # z - g / 3 = -1/3 leaves [0, 10] and clamps back to z: the clamped median 0 is optimal, R = 0
+    assert oracle.kkt_residual(np.array([0.0]), np.array([[-2.0], [-1.0], [5.0]]), np.array([1.0, 1.0, 1.0]),
+                               0.0, 10.0) == 0.0
+
+
+def test_kkt_residual_at_a_data_point_by_hand():
+    # z coincides with a_1 (weight w_1): the subgradient of w_1 ||z - a_1|| at z is the ball of
+    # radius w_1, so the residual uses g reduced in norm by w_1.  With a_2 = (4, 0), w_2 = 1 and
+    # a_3 = (0, -2), w_3 = 2, the other points give g = (-1, 0) + 2 (0, 1) = (-1, 2), ||g|| = sqrt 5.
+    z = np.zeros(2)
+    pts = np.array([[0.0, 0.0], [4.0, 0.0], [0.0, -2.0]])
+    # w_1 = 1.5 < sqrt 5: R = (sqrt 5 - 1.5) / (1.5 + 1 + 2) inside the box
+    w = np.array([1.5, 1.0, 2.0])
+    assert oracle.kkt_residual(z, pts, w, -10.0, 10.0) == pytest.approx((math.sqrt(5) - 1.5) / 4.5, rel=1e-14)
+    # w_1 = 3 >= sqrt 5: the data point is the minimiser (the vertex condition of the Fermat-Weber
+    # problem), so the residual is exactly 0; the objective confirms it is no worse than nearby points
+    w = np.array([3.0, 1.0, 2.0])
+    assert oracle.kkt_residual(z, pts, w, -10.0, 10.0) == 0.0
+    F0 = oracle.objective(z, pts, w)
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        assert oracle.objective(rng.normal(size=2) * 0.05, pts, w) >= F0
+    # just above the vertex threshold the point stops being optimal
+    w = np.array([math.sqrt(5) - 0.01, 1.0, 2.0])
+    assert oracle.kkt_residual(z, pts, w, -10.0, 10.0) == pytest.approx(0.01 / (math.sqrt(5) + 2.99), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# the threaded batch driver against the single-problem solver
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nthreads", [1, 4, 5])
+def test_em_admm_batch_equals_single_problem_runs(nthreads):
+    # B = 13 problems (not a multiple of the thread count), a start point per problem, the
+    # tolerance rule and a box other than [0, 255]: every output equals Algorithm 1 run on that
+    # problem alone from its float32 inputs widened to double, bit for bit.
+    rng = np.random.default_rng(21)
+    B, n, d = 13, 9, 4
+    pts = rng.uniform(0, 255, (B, n, d)).astype(np.float32)
+    w = rng.exponential(1.0, (B, n)).astype(np.float32)
+    z0 = rng.uniform(0, 255, (B, d)).astype(np.float32)
+    lo, hi, mu = 20.0, 190.0, 0.05
+    z, used, rp, rd = oracle.em_admm_batch(pts, w, lo, hi, mu, 400, z0=z0, tol=1e-3, check_every=3,
+                                           nthreads=nthreads)
+    stopped_early = 0
+    for b in range(B):
+        zb, ub, rpb, rdb = oracle.em_admm(pts[b].astype(np.float64), w[b].astype(np.float64), lo, hi, mu, 400,
+                                          z0=z0[b].astype(np.float64), tol=1e-3, check_every=3)
+        assert np.array_equal(z[b], zb)
+        assert used[b] == ub and rp[b] == rpb and rd[b] == rdb
+        stopped_early += ub < 400
+    assert stopped_early >= B // 2          # the tolerance path is exercised
+    # without a start point the batch starts from the projected weighted mean, as em_admm does
+    z, used, _, _ = oracle.em_admm_batch(pts, w, lo, hi, mu, 7, nthreads=nthreads)
+    for b in range(B):
+        zb, ub, _, _ = oracle.em_admm(pts[b].astype(np.float64), w[b].astype(np.float64), lo, hi, mu, 7)
+        assert np.array_equal(z[b], zb) and used[b] == ub
