@@ -272,8 +272,11 @@ int nlem_batch_config(nlem_ctx* ctx, char* buf, int len);
  *     and `stream`; images as for nlem_denoise_batch (patch 5 or 7, window^2 <= 441).
  *   - At most NLEM_NOALLOC_MAX_IMAGES images per call (-1 above that).  The array
  *     (about 18 KB) stays resident on every GPU that loads the library until the process exits.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture on that device.
+ *   - Each call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress, which allocates nothing), so the address stays right after
+ *     cudaDeviceReset or under a caller's own driver-API context.  The first call in a context
+ *     also loads the library's device code there: make that first call before any stream
+ *     capture on that device.
  *   - Every call shares the one array: the descriptors are rewritten and the counter is reset
  *     on each call, so calls whose GPU work overlaps (different streams, or different host
  *     threads, with no ordering between them) race and corrupt each other.  Order them.

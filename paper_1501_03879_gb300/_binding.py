@@ -520,6 +520,11 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
     n = len(images)
     if not (len(patches) == len(windows) == len(hs) == len(outs) == n):
         raise ValueError("one patch, window, h and output dict per image")
+    dev = images[0].device if n else torch.device("cuda", torch.cuda.current_device())
+    for k in range(n):
+        for t in (images[k], outs[k]["out"], outs[k].get("iters_used"), outs[k].get("residual")):
+            if t is not None and t.device != dev:
+                raise ValueError(f"image {k}: every image and output must be on {dev}")
     descs = (_ImageDesc * n)()
     for k, im in enumerate(images):
         _need(im, torch.float32, tuple(im.shape), f"images[{k}]")
@@ -533,8 +538,9 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
         d.H, d.W, d.pitch = H, W, pitch
         d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
     o = _options(tol, check_every, PREC_FP32, init)
-    _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
-                                                     _stream(images[0].device)))
+    with torch.cuda.device(dev):   # the library runs on the current device: make it the images'
+        _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box),
+                                                         ctypes.byref(o), _stream(dev)))
     return outs
 
 

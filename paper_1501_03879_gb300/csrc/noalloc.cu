@@ -9,7 +9,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/nlem.h"
@@ -18,16 +17,12 @@
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 constexpr size_t kQueueBytes = 256;   // the counter, padded so the descriptors stay aligned
 constexpr size_t kScratchBytes = kQueueBytes + sizeof(nlemk::BatchImage) * NLEM_NOALLOC_MAX_IMAGES;
 
 // Every GPU that loads the library holds this array until the process exits.  All calls on a
 // device share it; each call rewrites the descriptors and clears the counter.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-std::mutex g_mu;
-unsigned char* g_scratch_addr[kMaxDevices];   // device address of the array, per device
 
 int nerr(int code, const char* msg, int image = -1) {
   char buf[256];
@@ -51,10 +46,20 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
   if (iters < 0) return nerr(NLEM_ERR_INVALID, "iters must be >= 0");
   if (!std::isfinite(box.lo) || !std::isfinite(box.hi) || box.lo > box.hi)
     return nerr(NLEM_ERR_INVALID, "box must satisfy lo <= hi, both finite");
-  if (opt && (opt->check_every < 1 || !std::isfinite(opt->tol) || opt->precision != NLEM_PREC_FP32 ||
-              (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH) ||
-              opt->solver != NLEM_SOLVER_ADMM))
-    return nerr(NLEM_ERR_INVALID, "options: check_every >= 1, finite tol, FP32 precision, known init, EM-ADMM");
+  // the option checks of nlem_denoise_batch, with its error codes
+  if (opt) {
+    if (opt->check_every < 1) return nerr(NLEM_ERR_INVALID, "check_every must be >= 1");
+    if (!std::isfinite(opt->tol)) return nerr(NLEM_ERR_INVALID, "tol must be finite");
+    if (opt->precision != NLEM_PREC_FP32 && opt->precision != NLEM_PREC_BF16)
+      return nerr(NLEM_ERR_INVALID, "unknown precision");
+    if (opt->init != NLEM_INIT_WEIGHTED_MEAN && opt->init != NLEM_INIT_NOISY_PATCH)
+      return nerr(NLEM_ERR_INVALID, "unknown init");
+    if (opt->layout < NLEM_LAYOUT_AUTO || opt->layout > NLEM_LAYOUT_PAIR)
+      return nerr(NLEM_ERR_INVALID, "unknown layout");
+    if (opt->solver != NLEM_SOLVER_ADMM) return nerr(NLEM_ERR_INVALID, "the batched kernel runs EM-ADMM only");
+    if (opt->precision != NLEM_PREC_FP32)
+      return nerr(NLEM_ERR_UNSUPPORTED, "the batched kernel computes weights in FP32 only");
+  }
 
   // descriptors on the stack: this entry point makes no heap or device allocation of its own
   nlemk::BatchImage host[NLEM_NOALLOC_MAX_IMAGES];
@@ -89,20 +94,15 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return nerr(NLEM_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return nerr(NLEM_ERR_UNSUPPORTED, "device index too large");
-  unsigned char* scratch = nullptr;
-  {
-    // set-up, once per device, with that device current: the host-side name of the array is
-    // not a device address, so ask the runtime for the address on this device
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return nerr(NLEM_ERR_CUDA, cudaGetErrorString(e));
-      g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    scratch = g_scratch_addr[dev];
-  }
+  // The host-side name of the array is not a device address: ask the runtime for the address
+  // in the CURRENT context, on every call.  The address belongs to a context, not to a device:
+  // after cudaDeviceReset, or under a caller's own driver-API context on the same device, an
+  // address kept from an earlier call would be stale.  The lookup allocates nothing; the first
+  // call in a context also loads the library's device code there.
+  void* scratch_p = nullptr;
+  e = cudaGetSymbolAddress(&scratch_p, g_noalloc_scratch);
+  if (e != cudaSuccess) return nerr(NLEM_ERR_CUDA, cudaGetErrorString(e));
+  unsigned char* scratch = static_cast<unsigned char*>(scratch_p);
   auto* queue = reinterpret_cast<unsigned long long*>(scratch);
   auto* d_imgs = reinterpret_cast<nlemk::BatchImage*>(scratch + kQueueBytes);
   cudaStream_t s = (cudaStream_t)stream;

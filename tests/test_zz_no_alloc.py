@@ -64,3 +64,122 @@ def test_noalloc_rejects_oversized_batch(nl):
     with pytest.raises(nl.NlemError) as e:
         nl.nlem_denoise_batch_noalloc([g] * 257, [5] * 257, [5] * 257, [10.0] * 257, outs)
     assert e.value.code == -1
+
+
+def test_noalloc_tolerance_mode_and_residuals_match_batch(nl):
+    # the residual stopping rule (tol 1e-4 checked every 10 iterations) with the residual
+    # buffer: 7x7 patches run the same solver shape in both entry points, so the iteration
+    # counts agree pixel by pixel and the residuals to within rounding
+    specs = [(30, 26, 20.0, 7, 11), (21, 35, 40.0, 7, 15)]
+    ctx = nl.Context(0)
+    for call in range(2):
+        imgs, outs = _batch(5200 + 10 * call, specs)
+        for o, (H, W, *_ ) in zip(outs, specs):
+            o["residual"] = torch.full((H, W), -3.0, device=DEV)
+        ks = [k for *_, k, S in specs]
+        Ss = [S for *_, S in specs]
+        hs = [10 * s for _, _, s, _, _ in specs]
+        nl.nlem_denoise_batch_noalloc(imgs, ks, Ss, hs, outs, rho=1e-3, iters=300, tol=1e-4, check_every=10)
+        ref = nl.nlem_denoise_batch(imgs, ks, Ss, hs, rho=1e-3, iters=300, tol=1e-4, check_every=10, ctx=ctx)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o["iters_used"], r["iters_used"])
+            it = o["iters_used"].cpu().numpy()
+            stopped = it < 300
+            assert it.min() >= 10 and stopped.mean() > 0.5          # most pixels stop by the rule
+            assert rel_err(o["out"].cpu().numpy(), r["out"].cpu().numpy()).max() <= TOL
+            ro, rr = o["residual"].cpu().numpy(), r["residual"].cpu().numpy()
+            assert np.all(ro >= 0) and np.all(ro[stopped] < 1e-4)
+            assert np.abs(ro - rr).max() <= 1e-6
+
+
+def test_noalloc_error_codes_match_batch(nl):
+    # the same invalid or unsupported options give the same status as nlem_denoise_batch
+    import ctypes
+    from paper_1501_03879_gb300 import _binding as b
+    lib = nl.load_library()
+    g = torch.zeros((16, 16), device=DEV)
+    out = torch.zeros((16, 16), device=DEV)
+    desc = (b._ImageDesc * 1)()
+    desc[0].image, desc[0].out = g.data_ptr(), out.data_ptr()
+    desc[0].H = desc[0].W = desc[0].pitch = 16
+    desc[0].patch, desc[0].window, desc[0].h = 5, 5, 100.0
+    ctx = nl.Context(0)
+
+    def both(**kw):
+        o = b._Options()
+        lib.nlem_options_default(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        rc_a = lib.nlem_denoise_batch_noalloc(desc, 1, ctypes.c_float(1.0), 5, b._Box(0.0, 255.0), ctypes.byref(o), None)
+        rc_b = lib.nlem_denoise_batch(ctx.handle, desc, 1, ctypes.c_float(1.0), 5,
+                                      b._Box(0.0, 255.0), ctypes.byref(o), None)
+        torch.cuda.synchronize()
+        return rc_a, rc_b
+
+    assert both(precision=nl.PREC_BF16) == (-5, -5)
+    assert both(layout=7) == (-1, -1)
+    assert both(solver=nl.SOLVER_IRLS) == (-1, -1)
+    assert both(check_every=0) == (-1, -1)
+    assert both() == (0, 0)
+
+
+_RESET_CHILD = r"""
+import ctypes, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import synth
+from paper_1501_03879_gb300 import _binding as b
+lib = b.load_library()
+rt = None
+for line in open("/proc/self/maps"):
+    if "libcudart.so" in line:
+        rt = ctypes.CDLL(line.split()[-1])
+        break
+assert rt is not None, "libcudart not loaded by libnlem.so"
+H, W = 24, 30
+g = np.ascontiguousarray(synth.noisy_image(5300, H, W, 20.0)[0], dtype=np.float32)
+
+def run():
+    pi, po = ctypes.c_void_p(), ctypes.c_void_p()
+    assert rt.cudaMalloc(ctypes.byref(pi), ctypes.c_size_t(g.nbytes)) == 0
+    assert rt.cudaMalloc(ctypes.byref(po), ctypes.c_size_t(g.nbytes)) == 0
+    assert rt.cudaMemcpy(pi, g.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(g.nbytes), 1) == 0
+    d = (b._ImageDesc * 1)()
+    d[0].image, d[0].out = pi.value, po.value
+    d[0].H, d[0].W, d[0].pitch, d[0].patch, d[0].window, d[0].h = H, W, W, 7, 9, 200.0
+    o = b._Options()
+    lib.nlem_options_default(ctypes.byref(o))
+    rc = lib.nlem_denoise_batch_noalloc(d, 1, ctypes.c_float(0.8), 15, b._Box(0.0, 255.0), ctypes.byref(o), None)
+    assert rc == 0, lib.nlem_last_error()
+    out = np.empty_like(g)
+    assert rt.cudaMemcpy(out.ctypes.data_as(ctypes.c_void_p), po, ctypes.c_size_t(g.nbytes), 2) == 0
+    assert rt.cudaDeviceSynchronize() == 0
+    rt.cudaFree(pi); rt.cudaFree(po)
+    return out
+
+first = run()
+assert rt.cudaDeviceReset() == 0      # a new primary context: the array has a new address
+second = run()
+np.save(sys.argv[2], np.stack([g, first, second]))
+"""
+
+
+def test_noalloc_after_device_reset(nl, tmp_path):
+    # In a process of its own (torch is not used there): a call, cudaDeviceReset, and a call in
+    # the new context.  The array's address is looked up in the current context on every call,
+    # so the second call uses the new context's copy; both results equal the regular entry point.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = tmp_path / "reset.npy"
+    p = subprocess.run([sys.executable, "-c", _RESET_CHILD, root, str(res)], capture_output=True, text=True,
+                       timeout=300)
+    assert p.returncode == 0, p.stdout + p.stderr
+    g, first, second = np.load(res)
+    assert np.array_equal(first, second)
+    ref = nl.nlem_denoise_batch([torch.from_numpy(g).to(DEV)], [7], [9], [200.0], rho=0.8, iters=15,
+                                ctx=nl.Context(0))
+    torch.cuda.synchronize()
+    assert rel_err(first, ref[0]["out"].cpu().numpy()).max() <= TOL
