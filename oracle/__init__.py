@@ -96,11 +96,14 @@ def _load():
     lib.orc_weiszfeld.argtypes = [D, D, c_int, c_int, D, c_int, D, D]
     lib.orc_irls.argtypes = [D, D, c_int, c_int, c_double, c_double, D, c_double, c_int, D, D]
     lib.orc_em_admm_batch.argtypes = [F, F, c_ll, c_int, c_int, c_double, c_double, c_double, c_int,
-                                      F, c_double, c_int, D, I, D, D, c_int]
+                                      F, c_double, c_int, D, I, D, D, c_int, c_int]
     lib.orc_em_admm_batch.restype = c_int
     lib.orc_nlem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_double, c_int, c_double,
-                             c_double, c_double, c_int, c_int, c_int, LL, c_ll, D, I, D, D, I, D, c_int]
+                             c_double, c_double, c_int, c_int, c_int, LL, c_ll, D, I, D, D, I, D, c_int, c_int]
     lib.orc_nlem.restype = c_int
+    lib.orc_em_admm_wpen.argtypes = [D, D, c_int, c_int, c_double, c_double, c_double, c_int, D, c_double, c_int,
+                                     D, I, D, D]
+    lib.orc_em_admm_wpen.restype = c_int
     lib.orc_nlem_problem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_ll, c_int, D, D, D]
     lib.orc_nlem_problem.restype = c_int
     lib.orc_num_cores.restype = c_int
@@ -190,6 +193,25 @@ def em_admm_fast(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, eta
     return z, int(used[0]), float(rp[0]), float(rd[0]), int(rest[0])
 
 
+def em_admm_wpen(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1):
+    """Algorithm 1 with per-point penalties mu_k = mu w_k: prox radius 1/mu for every point, z the
+    projected w-weighted mean, residuals in the w-weighted norm.  Returns (z, iters_used, r_pri, r_dual)."""
+    pts, w = _f64(pts), _f64(w)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    n, d = pts.shape
+    z = np.empty(d)
+    used = np.zeros(1, dtype=np.int32)
+    rp = np.zeros(1)
+    rd = np.zeros(1)
+    z0a = _f64(z0) if z0 is not None else None
+    rc = _load().orc_em_admm_wpen(_dp(pts), _dp(w), n, d, float(lo), float(hi), float(mu), int(iters), _dp(z0a),
+                                  float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd))
+    if rc != 0:
+        raise MemoryError("oracle em_admm_wpen out of memory")
+    return z, int(used[0]), float(rp[0]), float(rd[0])
+
+
 def em_admm_set(pts, w, kind, a, b=None, r=0.0, mu=1.0, iters=100, z0=None, tol=0.0, check_every=1):
     """Algorithm 1 with the z-update projecting onto project_set's set (kind 1 or 2); the start is
     z0 as given, else the projected weighted mean.  Returns (z, iters_used, r_pri, r_dual)."""
@@ -269,9 +291,9 @@ def irls(pts, w, lo, hi, x0, eps, iters):
     return x, F[:iters]
 
 
-def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nthreads=0):
-    """Algorithm 1 on a float32 batch [B, n, d] (threads over problems).
-    Returns (z [B,d] float64, iters_used [B], r_pri [B], r_dual [B])."""
+def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nthreads=0, penalty=0):
+    """Algorithm 1 on a float32 batch [B, n, d] (threads over problems); penalty 1 solves each
+    problem with em_admm_wpen instead.  Returns (z [B,d] float64, iters_used [B], r_pri [B], r_dual [B])."""
     pts = np.ascontiguousarray(pts, dtype=np.float32)
     w = np.ascontiguousarray(w, dtype=np.float32)
     B, n, d = pts.shape
@@ -282,15 +304,16 @@ def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nt
     z0a = np.ascontiguousarray(z0, dtype=np.float32) if z0 is not None else None
     rc = _load().orc_em_admm_batch(_fp(pts), _fp(w), B, n, d, float(lo), float(hi), float(mu), int(iters),
                                    _fp(z0a), float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd),
-                                   int(nthreads))
+                                   int(nthreads), int(penalty))
     if rc != 0:
         raise MemoryError("oracle em_admm_batch failed")
     return z, used, rp, rd
 
 
 def nlem(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init_mode=0,
-         weight_mode=0, pixels=None, nthreads=0):
-    """NLEM (Sec. 3) on a float32 image.  Returns a dict with out (float64), iters_used,
+         weight_mode=0, pixels=None, nthreads=0, penalty=0):
+    """NLEM (Sec. 3) on a float32 image; penalty 1 solves each pixel's problem with em_admm_wpen
+    (per-point penalties mu_k = mu w_k).  Returns a dict with out (float64), iters_used,
     r_pri, r_dual, n (points per problem) and wsum (sum of weights), one entry per processed
     pixel (all pixels row-major, or the listed linear indices)."""
     img = np.ascontiguousarray(img, dtype=np.float32)
@@ -310,7 +333,7 @@ def nlem(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init
     pixp = pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None
     rc = _load().orc_nlem(_fp(img), H, W, int(k), int(S), float(h), float(mu), int(iters), float(lo), float(hi),
                           float(tol), int(check_every), int(init_mode), int(weight_mode), pixp, npix,
-                          _dp(out), _ip(used), _dp(rp), _dp(rd), _ip(nn), _dp(ws), int(nthreads))
+                          _dp(out), _ip(used), _dp(rp), _dp(rd), _ip(nn), _dp(ws), int(nthreads), int(penalty))
     if rc != 0:
         raise MemoryError("oracle nlem failed")
     res = dict(out=out, iters_used=used, r_pri=rp, r_dual=rd, n=nn, wsum=ws)

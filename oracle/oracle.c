@@ -172,6 +172,106 @@ void orc_weighted_mean_start(const double *pts, const double *w, int n, int d, d
  * The residuals of the last iteration run are always returned (0 if iters == 0).
  * Returns 0, or -1 if memory runs out.
  * ------------------------------------------------------------------------------------- */
+/* Algorithm 1 with a penalty per constraint, mu_k = mu * w_k (the augmented Lagrangian of Sec. 2
+ * with (mu_k / 2) ||x_k - z||^2 in place of (mu / 2) ||x_k - z||^2; Sec. 4 leaves the choice of
+ * penalty open).  The steps are those of Algorithm 1 with mu replaced by mu_k:
+ *   x_k = Psi_{w_k / mu_k}(z - y_k / mu_k, a_k)        prox radius w_k / mu_k = 1 / mu for every k
+ *   z   = P_C(sum_k mu_k (x_k + y_k / mu_k) / sum_k mu_k)   a weighted mean, weights w_k
+ *   y_k = y_k + mu_k (x_k - z)
+ * kept in the scaled multipliers u_k = y_k / mu_k (y_k = 0 at the start, so u_k = 0), which stay
+ * defined where w_k = 0: such a point has no penalty and no say in z.  If every weight is 0 the
+ * weights are taken as 1 (any z is then optimal).
+ * The stopping rule is the one of orc_em_admm in the norm the penalties define (each point's
+ * terms weighted by mu_k / mu = w_k, and n replaced by W = sum_k w_k):
+ *   r_pri  = sqrt(sum_k w_k ||x_k - z||^2) / max(sqrt(sum_k w_k ||x_k||^2), sqrt(W) ||z||, 1e-30)
+ *   r_dual = sqrt(W) ||z - z_prev|| / max(sqrt(sum_k w_k ||u_k||^2), 1e-30)
+ * Start, check schedule and outputs as orc_em_admm.  Returns 0, or -1 if memory runs out. */
+int orc_em_admm_wpen(const double *pts, const double *w, int n, int d, double lo, double hi, double mu,
+                     int iters, const double *z0, double tol, int check_every, double *z, int *iters_used,
+                     double *rpri, double *rdual) {
+  const size_t nd = (size_t)n * d;
+  double *x = (double *)malloc(sizeof(double) * nd);
+  double *u = (double *)calloc(nd, sizeof(double));
+  double *om = (double *)malloc(sizeof(double) * (size_t)n);
+  double *r = (double *)malloc(sizeof(double) * (size_t)d);
+  double *v = (double *)malloc(sizeof(double) * (size_t)d);
+  double *zprev = (double *)malloc(sizeof(double) * (size_t)d);
+  if (!x || !u || !om || !r || !v || !zprev) {
+    free(x); free(u); free(om); free(r); free(v); free(zprev);
+    return -1;
+  }
+  double W = 0.0;
+  for (int k = 0; k < n; ++k) W += w[k];
+  for (int k = 0; k < n; ++k) om[k] = W > 0.0 ? w[k] : 1.0;
+  if (!(W > 0.0)) W = (double)n;
+  if (z0) {
+    for (int q = 0; q < d; ++q) z[q] = z0[q];
+  } else {
+    orc_weighted_mean_start(pts, w, n, d, lo, hi, z);
+  }
+  if (check_every < 1) check_every = 1;
+  int t_done = 0;
+  double rp = 0.0, rd = 0.0;
+  for (int t = 1; t <= iters; ++t) {
+    for (int q = 0; q < d; ++q) r[q] = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double *xk = x + (size_t)k * d;
+      const double *uk = u + (size_t)k * d;
+      for (int q = 0; q < d; ++q) v[q] = z[q] - uk[q];
+      orc_prox(v, pts + (size_t)k * d, 1.0 / mu, d, xk);
+      for (int q = 0; q < d; ++q) r[q] += om[k] * (xk[q] + uk[q]);
+    }
+    for (int q = 0; q < d; ++q) {
+      zprev[q] = z[q];
+      z[q] = r[q] / W;
+    }
+    orc_project_box(z, d, lo, hi, z);
+    for (int k = 0; k < n; ++k) {
+      double *uk = u + (size_t)k * d;
+      const double *xk = x + (size_t)k * d;
+      for (int q = 0; q < d; ++q) uk[q] += xk[q] - z[q];
+    }
+    t_done = t;
+    int check = (t == iters) || (tol > 0.0 && (t % check_every) == 0);
+    if (check) {
+      double spr = 0.0, sx = 0.0, su = 0.0, zz = 0.0, dz = 0.0;
+      for (int k = 0; k < n; ++k) {
+        double pe = 0.0, px = 0.0, pu = 0.0;
+        for (int q = 0; q < d; ++q) {
+          double xq = x[(size_t)k * d + q];
+          double e = xq - z[q];
+          double uq = u[(size_t)k * d + q];
+          pe += e * e;
+          px += xq * xq;
+          pu += uq * uq;
+        }
+        spr += om[k] * pe;
+        sx += om[k] * px;
+        su += om[k] * pu;
+      }
+      for (int q = 0; q < d; ++q) {
+        zz += z[q] * z[q];
+        double e = z[q] - zprev[q];
+        dz += e * e;
+      }
+      double den_p = sqrt(sx);
+      double wzn = sqrt(W) * sqrt(zz);
+      if (wzn > den_p) den_p = wzn;
+      if (den_p < 1e-30) den_p = 1e-30;
+      double den_d = sqrt(su);
+      if (den_d < 1e-30) den_d = 1e-30;
+      rp = sqrt(spr) / den_p;
+      rd = sqrt(W) * sqrt(dz) / den_d;
+      if (tol > 0.0 && rp < tol && rd < tol) break;
+    }
+  }
+  if (iters_used) *iters_used = t_done;
+  if (rpri) *rpri = rp;
+  if (rdual) *rdual = rd;
+  free(x); free(u); free(om); free(r); free(v); free(zprev);
+  return 0;
+}
+
 /* Algorithm 1 with Nesterov-type momentum and restart (fast ADMM with restart; Goldstein et al.
  * 2014, the variant for objectives that are not strongly convex).  Steps (x, z, y) are those of
  * Algorithm 1, taken at the extrapolated z_hat and y_hat.  After each step the combined residual
@@ -478,6 +578,7 @@ typedef struct {
   int *iters_used;
   double *rpri, *rdual;
   int status;
+  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen) */
 } batch_job;
 
 static void *batch_worker(void *arg) {
@@ -497,8 +598,11 @@ static void *batch_worker(void *arg) {
     }
     int used = 0;
     double rp = 0, rd = 0;
-    if (orc_em_admm(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
-                    J->z + (size_t)b * d, &used, &rp, &rd) != 0) {
+    int rc = J->penalty ? orc_em_admm_wpen(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol,
+                                           J->check_every, J->z + (size_t)b * d, &used, &rp, &rd)
+                        : orc_em_admm(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
+                                      J->z + (size_t)b * d, &used, &rp, &rd);
+    if (rc != 0) {
       J->status = -1;
       break;
     }
@@ -521,14 +625,14 @@ int orc_num_cores(void) { return resolve_threads(0); }
 int orc_em_admm_batch(const float *pts, const float *w, long long B, int n, int d, double lo,
                       double hi, double mu, int iters, const float *z0, double tol,
                       int check_every, double *z, int *iters_used, double *rpri,
-                      double *rdual, int nthreads) {
+                      double *rdual, int nthreads, int penalty) {
   int T = resolve_threads(nthreads);
   if ((long long)T > B) T = (int)(B > 0 ? B : 1);
   pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)T);
   batch_job *jobs = (batch_job *)malloc(sizeof(batch_job) * (size_t)T);
   for (int i = 0; i < T; ++i) {
     batch_job J = {pts, w, z0, B, n, d, iters, check_every, T, i, lo, hi, mu, tol,
-                   z, iters_used, rpri, rdual, 0};
+                   z, iters_used, rpri, rdual, 0, penalty};
     jobs[i] = J;
     pthread_create(&th[i], NULL, batch_worker, &jobs[i]);
   }
@@ -583,6 +687,7 @@ typedef struct {
   double *out, *rpri, *rdual, *wsum_out;
   int *iters_used, *n_out;
   int status;
+  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen) */
 } nlem_job;
 
 /* Patch of g centred at (r, c), reflect-padded, row-major k x k, as double. */
@@ -645,8 +750,11 @@ static void *nlem_worker(void *arg) {
     }
     int used = 0;
     double rp = 0, rd = 0;
-    if (orc_em_admm(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
-                    z, &used, &rp, &rd) != 0) {
+    int rc = J->penalty ? orc_em_admm_wpen(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol,
+                                           J->check_every, z, &used, &rp, &rd)
+                        : orc_em_admm(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
+                                      z, &used, &rp, &rd);
+    if (rc != 0) {
       J->status = -1;
       break;
     }
@@ -669,7 +777,7 @@ done:
 int orc_nlem(const float *img, int H, int W, int k, int S, double h, double mu, int iters,
              double lo, double hi, double tol, int check_every, int init_mode, int weight_mode,
              const long long *pix, long long npix, double *out, int *iters_used, double *rpri,
-             double *rdual, int *n_out, double *wsum_out, int nthreads) {
+             double *rdual, int *n_out, double *wsum_out, int nthreads, int penalty) {
   int T = resolve_threads(nthreads);
   long long total = pix ? npix : (long long)H * W;
   if ((long long)T > total) T = (int)(total > 0 ? total : 1);
@@ -677,7 +785,7 @@ int orc_nlem(const float *img, int H, int W, int k, int S, double h, double mu, 
   nlem_job *jobs = (nlem_job *)malloc(sizeof(nlem_job) * (size_t)T);
   for (int i = 0; i < T; ++i) {
     nlem_job J = {img, H, W, k, S, iters, check_every, init_mode, weight_mode, T, i,
-                  h, mu, lo, hi, tol, pix, npix, out, rpri, rdual, wsum_out, iters_used, n_out, 0};
+                  h, mu, lo, hi, tol, pix, npix, out, rpri, rdual, wsum_out, iters_used, n_out, 0, penalty};
     jobs[i] = J;
     pthread_create(&th[i], NULL, nlem_worker, &jobs[i]);
   }
