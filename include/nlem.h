@@ -41,6 +41,9 @@ extern "C" {
 #define NLEM_SOLVER_IRLS 1          /* IRLS on the smooth surrogate of Eq. 2 (Sec. 1), the comparison
                                        method of Sec. 3 (nlem_denoise only) */
 
+#define NLEM_PENALTY_UNIFORM 0       /* one penalty mu = rho for every constraint x_k = z: Algorithm 1 */
+#define NLEM_PENALTY_WEIGHTED 1      /* a penalty per constraint, mu_k = rho * w_k (see nlem_options) */
+
 #define NLEM_LAYOUT_AUTO 0          /* nlem_denoise picks the problem-to-CTA layout */
 #define NLEM_LAYOUT_PIXEL 1         /* one pixel's problem per CTA */
 #define NLEM_LAYOUT_PAIR 2          /* two horizontally adjacent pixels per CTA, sharing the points
@@ -67,6 +70,16 @@ typedef struct {
   int solver;         /* NLEM_SOLVER_* (default ADMM).  IRLS is taken by nlem_denoise and
                          nlem_denoise_host only; every other entry point returns -1 for it */
   float irls_eps;     /* epsilon of the surrogate (Eq. 2), >= 1e-30 (default 1e-6) */
+  int penalty;        /* NLEM_PENALTY_* (default UNIFORM).  WEIGHTED solves problem (1) with the
+                         ADMM steps of Algorithm 1 under a penalty mu_k = rho * w_k on each
+                         constraint x_k = z of the splitting (Sec. 2; Sec. 4 leaves the penalty
+                         choice open): every prox radius w_k / mu_k becomes 1 / rho, the z-update
+                         becomes the projected w-weighted mean of x_k + y_k / mu_k, and the
+                         stopping rule's residuals are taken in the w-weighted norm (each point's
+                         terms times w_k, n replaced by sum_k w_k).  Compiled for em_solve_batch
+                         (and em_solve, em_solve_batch_host) with d = 49 and for nlem_denoise,
+                         nlem_denoise_host and nlem_denoise_ex with 7x7 patches on the one-pixel
+                         layout; -5 elsewhere (-1 with IRLS) */
 } nlem_options;
 
 void nlem_options_default(nlem_options* opt);

@@ -17,6 +17,8 @@ from ._binding import (  # noqa: F401
     LAYOUT_AUTO,
     LAYOUT_PAIR,
     LAYOUT_PIXEL,
+    PENALTY_UNIFORM,
+    PENALTY_WEIGHTED,
     PREC_BF16,
     PREC_FP32,
     SOLVER_ADMM,

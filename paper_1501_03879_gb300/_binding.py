@@ -17,6 +17,8 @@ SOLVER_IRLS = 1
 LAYOUT_AUTO = 0
 LAYOUT_PIXEL = 1
 LAYOUT_PAIR = 2
+PENALTY_UNIFORM = 0
+PENALTY_WEIGHTED = 1
 
 _ERRNAMES = {-1: "NLEM_ERR_INVALID", -2: "NLEM_ERR_CUDA", -3: "NLEM_ERR_OOM", -4: "NLEM_ERR_TIMEOUT",
              -5: "NLEM_ERR_UNSUPPORTED"}
@@ -46,7 +48,7 @@ class _Set(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("layout", ctypes.c_int),
-                ("solver", ctypes.c_int), ("irls_eps", ctypes.c_float)]
+                ("solver", ctypes.c_int), ("irls_eps", ctypes.c_float), ("penalty", ctypes.c_int)]
 
 
 _lib = None
@@ -170,7 +172,7 @@ def _stream(device):
 
 
 def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False,
-             layout=0, solver=None, irls_eps=None):
+             layout=0, solver=None, irls_eps=None, penalty=PENALTY_UNIFORM):
     o = _Options()
     load_library().nlem_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -183,6 +185,7 @@ def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEA
         o.solver = int(solver)
     if irls_eps is not None:
         o.irls_eps = float(irls_eps)
+    o.penalty = int(penalty)
     return o
 
 
@@ -237,8 +240,9 @@ def em_solve(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, out=None, ct
 
 
 def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
-                   fp64_check=False, ctx: Context | None = None, out=None):
-    """Algorithm 1 on B problems: points [B, n, d], weights [B, n] (float32 CUDA).
+                   fp64_check=False, ctx: Context | None = None, out=None, penalty=PENALTY_UNIFORM):
+    """Algorithm 1 on B problems: points [B, n, d], weights [B, n] (float32 CUDA).  penalty:
+    PENALTY_UNIFORM (Algorithm 1) or PENALTY_WEIGHTED (mu_k = rho w_k; d = 49).
     Returns dict(x [B,d], iters_used [B] int32, residual [B], obj64/kkt64 [B] float64 if fp64_check)."""
     import torch
     B, n, d = points.shape
@@ -262,7 +266,7 @@ def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=Non
     if fp64_check:
         obj = torch.empty(B, dtype=torch.float64, device=dev)
         kkt = torch.empty(B, dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, fp64_check=fp64_check)
+    o = _options(tol, check_every, fp64_check=fp64_check, penalty=penalty)
     _check(load_library().em_solve_batch(c.handle, _ptr(points), _ptr(weights), B, n, d, _Box(*box), float(rho),
                                          int(iters), _ptr(x0), ctypes.byref(o), _ptr(x), _ptr(used), _ptr(resid),
                                          _ptr(obj), _ptr(kkt), _stream(dev)))
@@ -326,7 +330,7 @@ def _host_ptr(t, dtype, shape, name):
 
 
 def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
-                        chunk=0, ctx: Context | None = None, out=None, device=0):
+                        chunk=0, ctx: Context | None = None, out=None, device=0, penalty=PENALTY_UNIFORM):
     """Algorithm 1 on B problems held in HOST memory: points [B, n, d] and weights [B, n] (CPU float32
     tensors, ideally pinned).  The library copies them in chunks of `chunk` problems (0 = about 1 GiB),
     overlapping the copy of each chunk with the solve of the previous one, and copies the results
@@ -348,7 +352,7 @@ def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x
     resid = res.get("residual")
     if resid is None:
         resid = torch.empty(B, dtype=torch.float32, pin_memory=pin)
-    o = _options(tol, check_every)
+    o = _options(tol, check_every, penalty=penalty)
     _check(load_library().em_solve_batch_host(c.handle, pp, wp, B, n, d, _Box(*box), float(rho), int(iters), x0p,
                                               ctypes.byref(o), int(chunk),
                                               _host_ptr(x, torch.float32, (B, d), "x"),
@@ -360,7 +364,7 @@ def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x
 
 def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                  precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None,
-                 out=None, layout=LAYOUT_AUTO, solver=SOLVER_ADMM, irls_eps=1e-6):
+                 out=None, layout=LAYOUT_AUTO, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM):
     """NLEM (Sec. 3) of a float32 CUDA image [H, W].  Returns dict(out [H,W], iters_used,
     residual[, obj64, kkt64]).  layout: LAYOUT_AUTO, LAYOUT_PIXEL (one pixel per CTA) or
     LAYOUT_PAIR (two adjacent pixels per CTA; patch 7, window <= 21, FP32).  solver: SOLVER_ADMM
@@ -384,7 +388,7 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
     if fp64_check:
         obj = torch.empty((H, W), dtype=torch.float64, device=dev)
         kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, precision, init, fp64_check, layout, solver, irls_eps)
+    o = _options(tol, check_every, precision, init, fp64_check, layout, solver, irls_eps, penalty)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
@@ -434,7 +438,7 @@ def nlem_denoise_color(image, patch=5, window=21, h=200.0, rho=1.0, iters=100, b
 
 def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
                       check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, ctx: Context | None = None,
-                      out=None, iters_used=None, device=0, solver=SOLVER_ADMM, irls_eps=1e-6):
+                      out=None, iters_used=None, device=0, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM):
     """NLEM on HOST buffers (numpy float32 [H, W] or CPU torch tensor, ideally pinned):
     copies in, denoises and copies out inside the library.  Returns the host output."""
     import numpy as np
@@ -449,7 +453,7 @@ def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, bo
     c = ctx or _ctx(torch.device("cuda", device))
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, pin_memory=img_t.is_pinned())
-    o = _options(tol, check_every, precision, init, solver=solver, irls_eps=irls_eps)
+    o = _options(tol, check_every, precision, init, solver=solver, irls_eps=irls_eps, penalty=penalty)
     ip = ctypes.c_void_p(iters_used.data_ptr()) if iters_used is not None else None
     _check(load_library().nlem_denoise_host(c.handle, ctypes.c_void_p(img_t.data_ptr()), H, W, int(patch),
                                             int(window), float(h), float(rho), int(iters), _Box(*box),
@@ -679,7 +683,7 @@ def nlem_features(image, patch=7, window=21, h=200.0, pixels=None, ctx: Context 
 
 def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                     init=INIT_WEIGHTED_MEAN, pixels=None, x0=None, rho_pix=None, z_out=False, ctx: Context | None = None,
-                    out=None):
+                    out=None, penalty=PENALTY_UNIFORM):
     """NLEM on a pixel list with optional per-pixel start points / penalties (indexed by
     linear pixel) and the full solution patches.  Returns dict(out, iters_used, residual[, z])."""
     import torch
@@ -703,7 +707,7 @@ def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=
         if z is None:
             z = torch.zeros((H * W, d), dtype=torch.float32, device=dev)
     n = pixels.numel() if pixels is not None else 0
-    opts = _options(tol, check_every, PREC_FP32, init)
+    opts = _options(tol, check_every, PREC_FP32, init, penalty=penalty)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise_ex(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                           int(iters), _Box(*box), ctypes.byref(opts), _ptr(pixels), n, _ptr(x0),

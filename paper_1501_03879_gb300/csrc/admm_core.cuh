@@ -378,13 +378,38 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
 // lanes of a point split the rsqrt of the step s.  The standalone batch kernel measured 3.6%
 // faster with it; the NLEM kernels of one pixel per CTA measured 2-5% slower, so they do not
 // take it (the register allocation decides).
-template <class C, bool SPLIT = false, class X = NoExchange, class PJ = ScalarBox>
+// WPEN: per-point penalties mu_k = mu w_k (a penalty per constraint in the augmented Lagrangian
+// of Sec. 2).  lam then holds the weights w_j (zero for inactive slots) instead of w_j / mu:
+//   s_k = min(1, (1/mu) / ||e_k||) (the prox radius w_k / mu_k = 1/mu; 0 where w_k = 0, whose
+//   terms carry weight 0 everywhere), z+ = P_C(z - sum_k w_k g_k / W) with W = sum_k w_k, and
+//   the residuals of the stopping rule in the w-weighted norm (n -> W, each point's terms
+//   times w_k), so the reformulation above holds with every sum over k weighted by w_k.
+// If every weight is zero the weights are taken as 1.
+template <class C, bool SPLIT = false, class X = NoExchange, class PJ = ScalarBox, bool WPEN = false>
 __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm, const PJ& pj = PJ()) {
   static_assert(!SPLIT || C::G == 2, "the split rsqrt pairs the two lanes of a point");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
   const bool last = (g == C::G - 1);
-  const float inv_n = 1.f / (float)n;
-  const float fn = (float)n;
+  float inv_n = 1.f / (float)n;
+  float fn = (float)n;
+  if constexpr (WPEN) {   // W = sum_k w_k, the count the weighted sums divide by
+    __syncthreads();
+    if (t < 32) {
+      float sw = 0.f;
+      for (int j = lane; j < C::CAP; j += 32) sw += sm.lam[j];
+      sw = warp_sum(sw);
+      if (lane == 0) sm.scal[8] = sw;
+    }
+    __syncthreads();
+    float W = sm.scal[8];
+    if (!(W > 0.f)) {
+      for (int j = t; j < n; j += C::NT) sm.lam[j] = 1.f;
+      W = (float)n;
+      __syncthreads();
+    }
+    inv_n = 1.f / W;
+    fn = W;
+  }
 
   // state h as coordinate pairs (packed FP32: one FADD2 / FFMA2 serves two slots) plus the
   // single last slot when Q is odd
@@ -467,8 +492,11 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
         const float r2 = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, C::LPG);
         const int p = 2 * k + (up ? 1 : 0);
         const bool valid = p < C::P;
-        sh[k] = valid ? fminf(1.f, sm.lam[pg + (valid ? p : 0) * C::NG] * rsqrtf(r2)) : 0.f;
-        gs = fmaf(sh[k] * sh[k], valid ? r2 : 0.f, gs);   // each point's ||g_k||^2 once, by its owner
+        const float lj = sm.lam[pg + (valid ? p : 0) * C::NG];
+        const float lam_k = WPEN ? (lj > 0.f ? prm.inv_mu : 0.f) : lj;
+        sh[k] = valid ? fminf(1.f, lam_k * rsqrtf(r2)) : 0.f;
+        // each point's ||g_k||^2 once, by its owner (times w_k with per-point penalties)
+        gs = fmaf((WPEN ? lj : 1.f) * sh[k] * sh[k], valid ? r2 : 0.f, gs);
       }
 #pragma unroll
       for (int k = 0; k < PH; ++k) {
@@ -482,11 +510,16 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 #pragma unroll
       for (int p = 0; p < C::P; ++p) {
         const float r2 = s[p];
-        s[p] = fminf(1.f, sm.lam[pg + p * C::NG] * rsqrtf(r2));
-        gs = fmaf(s[p] * s[p], r2, gs);
+        const float lj = sm.lam[pg + p * C::NG];
+        s[p] = fminf(1.f, (WPEN ? (lj > 0.f ? prm.inv_mu : 0.f) : lj) * rsqrtf(r2));
+        gs = fmaf((WPEN ? lj : 1.f) * s[p] * s[p], r2, gs);
       }
       if (g != 0) gs = 0.f;    // each point's ||g_k||^2 counted once, by its slice-0 lane
     }
+    // the factor of g_k in the sums over k: s_k, or w_k s_k with per-point penalties
+    float ws[C::P];
+#pragma unroll
+    for (int p = 0; p < C::P; ++p) ws[p] = WPEN ? sm.lam[pg + p * C::NG] * s[p] : s[p];
     float dd = 0.f;            // sum_k ||h_k(t) - h_k(t+1)||^2 over this lane's slots
     if (check) {
       // ||(1-s) e + a - c||^2 in a pass of its own; the fences keep the compiler from
@@ -499,6 +532,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
         const float oms = 1.f - s[p];
         const float2 oms2 = make_float2(oms, oms);
         float2 dd2 = make_float2(0.f, 0.f);
+        float dd1 = 0.f;
 #pragma unroll
         for (int i = 0; i < C::NQA; ++i) {
           const float4 a4 = load_quad<C>(arow, i, last);
@@ -513,11 +547,18 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
               dd2 = __ffma2_rn(dq2, dq2, dd2);
             } else if (q0 < C::Q) {
               const float dq = fmaf(oms, h1[p], a2.x - c2.x);
-              dd = fmaf(dq, dq, dd);
+              if constexpr (WPEN)
+                dd1 = fmaf(dq, dq, dd1);
+              else
+                dd = fmaf(dq, dq, dd);
             }
           }
         }
-        dd += dd2.x + dd2.y;
+        // per-point penalties weight the point's term by w_k
+        if constexpr (WPEN)
+          dd = fmaf(sm.lam[pg + p * C::NG], dd1 + (dd2.x + dd2.y), dd);
+        else
+          dd += dd2.x + dd2.y;
         asm volatile("" ::: "memory");
       }
     }
@@ -544,16 +585,16 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
               const int ni = lin / C::P, np = lin % C::P;
               if (ni < C::NQA) a_n2 = load_quad<C>(abase + np * C::NG * C::DP, ni, last);
             }
-            const float2 sp2 = make_float2(s[p], s[p]);
+            const float2 sp2 = make_float2(s[p], s[p]), wp2 = make_float2(ws[p], ws[p]);
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
               const int q0 = 4 * i + 2 * jh;
               const float2 na2 = jh == 0 ? make_float2(-a4.x, -a4.y) : make_float2(-a4.z, -a4.w);
               if (q0 + 1 < C::Q) {
-                accp[jh] = __ffma2_rn(sp2, h2[p][q0 / 2], accp[jh]);
+                accp[jh] = __ffma2_rn(wp2, h2[p][q0 / 2], accp[jh]);
                 h2[p][q0 / 2] = __ffma2_rn(sp2, h2[p][q0 / 2], na2);
               } else if (q0 < C::Q) {
-                acc1 = fmaf(s[p], h1[p], acc1);
+                acc1 = fmaf(ws[p], h1[p], acc1);
                 h1[p] = fmaf(s[p], h1[p], na2.x);
               }
             }

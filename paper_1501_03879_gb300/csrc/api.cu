@@ -61,7 +61,18 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
         return fail(NLEM_ERR_INVALID, "irls_eps must be finite and >= 1e-30 (got %g)", opt->irls_eps);
       if (opt->tol > 0.f) return fail(NLEM_ERR_INVALID, "IRLS runs a fixed number of steps: tol must be <= 0");
     }
+    if (opt->penalty != NLEM_PENALTY_UNIFORM && opt->penalty != NLEM_PENALTY_WEIGHTED)
+      return fail(NLEM_ERR_INVALID, "unknown penalty %d", opt->penalty);
+    if (opt->penalty == NLEM_PENALTY_WEIGHTED && opt->solver == NLEM_SOLVER_IRLS)
+      return fail(NLEM_ERR_INVALID, "per-point penalties belong to EM-ADMM, not IRLS");
   }
+  return NLEM_OK;
+}
+
+// Entry points whose kernels take one penalty for every point (Algorithm 1) only.
+int uniform_penalty_only(const nlem_options* opt, const char* who) {
+  if (opt && opt->penalty != NLEM_PENALTY_UNIFORM)
+    return fail(NLEM_ERR_UNSUPPORTED, "%s solves with one penalty for every point only", who);
   return NLEM_OK;
 }
 
@@ -199,7 +210,10 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
   L.kkt64 = chk ? kkt64 : nullptr;
   L.sm_count = ctx->sm_count;
   L.stream = (cudaStream_t)stream;
+  L.penalty = opt ? opt->penalty : NLEM_PENALTY_UNIFORM;
   int e = nlemk::launch_em_batch(L);
+  if (e == -1 && L.penalty != NLEM_PENALTY_UNIFORM)
+    return fail(NLEM_ERR_UNSUPPORTED, "per-point penalties are compiled for d = 49 (got d = %d)", d);
   if (e == -1) return fail(NLEM_ERR_UNSUPPORTED, "no kernel shape for n = %d, d = %d", n, d);
   if (e != 0) return cuda_fail((cudaError_t)e, "em_solve_batch launch");
   return NLEM_OK;
@@ -212,6 +226,7 @@ int em_solve_batch_set(nlem_ctx* ctx, const float* points, const float* weights,
   int rc = check_common(ctx, any, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "em_solve_batch_set"))) return rc;
+  if ((rc = uniform_penalty_only(opt, "em_solve_batch_set"))) return rc;
   if (!set) return fail(NLEM_ERR_INVALID, "set is NULL");
   if (set->kind == NLEM_SET_COORD_BOXES) {
     if (!set->lo || !set->hi) return fail(NLEM_ERR_INVALID, "coordinate boxes need lo and hi");
@@ -400,6 +415,9 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   L.max_items = 0;
   L.ex = nlemk::PixelExtra{};
   L.layout = opt ? opt->layout : NLEM_LAYOUT_AUTO;
+  L.penalty = opt ? opt->penalty : NLEM_PENALTY_UNIFORM;
+  if (L.penalty != NLEM_PENALTY_UNIFORM && (patch != 7 || L.layout == NLEM_LAYOUT_PAIR))
+    return fail(NLEM_ERR_UNSUPPORTED, "per-point penalties are compiled for 7x7 patches on the one-pixel layout");
   if (opt && opt->precision == NLEM_PREC_BF16) {
     // cross terms on the tensor cores into the weight table, then the solver reads it
     const size_t need = (size_t)H * W * (size_t)window * window;
@@ -442,6 +460,7 @@ int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitc
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "nlem_denoise_color"))) return rc;
+  if ((rc = uniform_penalty_only(opt, "nlem_denoise_color"))) return rc;
   if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1 (got %dx%d)", H, W);
   if (pitch < W) return fail(NLEM_ERR_INVALID, "pitch %d < W %d", pitch, W);
   if (channels < 1) return fail(NLEM_ERR_INVALID, "channels must be >= 1 (got %d)", channels);
@@ -685,6 +704,7 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "nlem_denoise_batch"))) return rc;
+  if ((rc = uniform_penalty_only(opt, "nlem_denoise_batch"))) return rc;
   if (count < 0) return fail(NLEM_ERR_INVALID, "count must be >= 0");
   if (count == 0) return NLEM_OK;
   if (!images) return fail(NLEM_ERR_INVALID, "images is NULL");

@@ -21,6 +21,7 @@ struct EmLaunch {
   double* kkt64;
   int sm_count;
   cudaStream_t stream;
+  int penalty = 0;       // NLEM_PENALTY_* (1: per-point penalties mu_k = rho w_k)
 };
 
 // Optional per-pixel inputs and outputs of the NLEM kernel (all NULL = plain NLEM).
@@ -50,6 +51,7 @@ struct NlemLaunch {
   int layout;            // NLEM_LAYOUT_* of the options (0 = auto)
   int sm_count;
   cudaStream_t stream;
+  int penalty = 0;       // NLEM_PENALTY_* (1: per-point penalties mu_k = rho w_k)
 };
 
 // Multichannel NLEM: planar image, channel c at img + c*cstride, out [channels][H][W].
@@ -88,6 +90,10 @@ bool nlem_pair_eligible(const NlemLaunch& L);
 int launch_nlem_pair_k7(const NlemLaunch& L);
 int em_capacity(int d);
 int nlem_capacity(int patch);
+// Per-point penalties mu_k = rho w_k (compiled for d = 49 standalone problems and 7x7 NLEM
+// patches on the one-pixel layout); -1 for any other shape.
+int launch_em_wpen_d49(const EmLaunch& L);
+int launch_nlem_wpen_k7(const NlemLaunch& L);
 // Standalone batch over per-coordinate boxes (kind 1: a = lo, b = hi, device [d]) or the ball
 // ||x - a|| <= r (kind 2: a = centre, device [d]); its point capacity for dimension d.
 int launch_em_set(const EmLaunch& L, int kind, const float* a, const float* b, float r);

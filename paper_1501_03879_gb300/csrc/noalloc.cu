@@ -56,7 +56,11 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
       return nerr(NLEM_ERR_INVALID, "unknown init");
     if (opt->layout < NLEM_LAYOUT_AUTO || opt->layout > NLEM_LAYOUT_PAIR)
       return nerr(NLEM_ERR_INVALID, "unknown layout");
+    if (opt->penalty != NLEM_PENALTY_UNIFORM && opt->penalty != NLEM_PENALTY_WEIGHTED)
+      return nerr(NLEM_ERR_INVALID, "unknown penalty");
     if (opt->solver != NLEM_SOLVER_ADMM) return nerr(NLEM_ERR_INVALID, "the batched kernel runs EM-ADMM only");
+    if (opt->penalty != NLEM_PENALTY_UNIFORM)
+      return nerr(NLEM_ERR_UNSUPPORTED, "the batched kernel takes one penalty for every point only");
     if (opt->precision != NLEM_PREC_FP32)
       return nerr(NLEM_ERR_UNSUPPORTED, "the batched kernel computes weights in FP32 only");
   }

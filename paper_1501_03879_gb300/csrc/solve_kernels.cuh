@@ -15,7 +15,8 @@ namespace nlemk {
 // shared-memory point rows, one problem per CTA iteration
 // ------------------------------------------------------------------------------------------
 // PJ: the constraint set (ScalarBox = the box of SolveParams; CoordBoxes, Ball from admm_core.cuh).
-template <class C, class PJ = ScalarBox>
+// WPEN: per-point penalties mu_k = mu w_k (admm_iterate).
+template <class C, class PJ = ScalarBox, bool WPEN = false>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, long long B, int n,
                 int d, SolveParams prm, const float* __restrict__ x0, float* __restrict__ x_out,
@@ -49,7 +50,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       if (j < n) {
         const float w = __ldg(Wt + j);
         bad |= !(w >= 0.f) || !isfinite(w);
-        lam = w * prm.inv_mu;
+        lam = WPEN ? w : w * prm.inv_mu;
       }
       sm.lam[j] = lam;
     }
@@ -92,7 +93,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       }
       weighted_mean_start<C, NoExchange, PJ>(sm, wreg, n, dd, prm, pj);
     }
-    admm_iterate<C, C::G == 2, NoExchange, PJ>(sm, n, dd, prm, pj);
+    admm_iterate<C, C::G == 2, NoExchange, PJ, WPEN>(sm, n, dd, prm, pj);
     for (int q = t; q < dd; q += C::NT) {
       const int sg = q / C::Q, i = q - sg * C::Q;
       x_out[(size_t)b * dd + q] = sm.zv[sg * C::QA + i];
@@ -126,8 +127,9 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
 // reflect-padded image around the clipped search window -> patch rows in shared memory ->
 // weights exp(-||P_i-P_j||^2/h^2) -> start point -> EM-ADMM -> centre coordinate.
 // IRLS: the surrogate solver of Eq. 2 in place of EM-ADMM (NLEM-IRLS, the comparison method of
-// Sec. 3).  Ends with a barrier, so the caller may start the next pixel at once.
-template <class C, int K, bool IRLS = false>
+// Sec. 3).  WPEN: EM-ADMM with per-point penalties mu_k = mu w_k (admm_iterate).  Ends with a
+// barrier, so the caller may start the next pixel at once.
+template <class C, int K, bool IRLS = false, bool WPEN = false>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
@@ -218,7 +220,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
       float w = j < n ? expf(-Dp * inv_h2) : 0.f;
       if (wtab) w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;   // precomputed (BF16 mode)
       wreg[p] = w;
-      if (g == 0) sm.lam[j] = IRLS ? w : w * pp.inv_mu;
+      if (g == 0) sm.lam[j] = (IRLS || WPEN) ? w : w * pp.inv_mu;
     }
   }
   if (ex.x0) {   // caller's start point, projected onto C
@@ -249,7 +251,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   if constexpr (IRLS)
     irls_iterate<C>(sm, n, C::D, pp);
   else
-    admm_iterate<C>(sm, n, C::D, pp);
+    admm_iterate<C, false, NoExchange, ScalarBox, WPEN>(sm, n, C::D, pp);
   if (ex.z_out) {
     for (int q = t; q < C::D; q += C::NT)
       ex.z_out[pix * (long long)C::D + q] = sm.zv[(q / C::Q) * C::QA + (q % C::Q)];
@@ -281,7 +283,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   __syncthreads();
 }
 
-template <class C, int K, bool IRLS = false>
+template <class C, int K, bool IRLS = false, bool WPEN = false>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
@@ -293,17 +295,17 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
   const long long items = pix_list ? *n_list : (long long)H * W;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const long long pix = pix_list ? (long long)pix_list[it] : it;
-    nlem_pixel<C, K, IRLS>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid, obj64, kkt64,
-                     wtab, ex);
+    nlem_pixel<C, K, IRLS, WPEN>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out, iters_used, resid,
+                                 obj64, kkt64, wtab, ex);
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <class C, class PJ = ScalarBox>
+template <class C, class PJ = ScalarBox, bool WPEN = false>
 inline int launch_em(const EmLaunch& L, int grid_mult, const PJ& pj = PJ()) {
-  auto kern = em_batch_kernel<C, PJ>;
+  auto kern = em_batch_kernel<C, PJ, WPEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
   if (e != cudaSuccess) return (int)e;
   long long grid = L.B;
@@ -315,10 +317,10 @@ inline int launch_em(const EmLaunch& L, int grid_mult, const PJ& pj = PJ()) {
   return (int)cudaGetLastError();
 }
 
-template <class C, int K, bool IRLS = false>
+template <class C, int K, bool IRLS = false, bool WPEN = false>
 inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
   if ((L.S + K - 1) * (L.S + K - 1) > C::SZ_WRED) return -1;   // tile must fit its region
-  auto kern = nlem_kernel<C, K, IRLS>;
+  auto kern = nlem_kernel<C, K, IRLS, WPEN>;
   const size_t smem = C::SMEM_BYTES;
   if (smem > 232448) return -1;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

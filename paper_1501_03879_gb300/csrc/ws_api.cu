@@ -104,6 +104,7 @@ nlemk::NlemLaunch base_launch(nlem_ctx* ctx, const float* image, int H, int W, i
   L.prm.check_every = opt ? opt->check_every : 1;
   L.prm.d = patch * patch;
   L.init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
+  L.penalty = opt ? opt->penalty : NLEM_PENALTY_UNIFORM;
   L.sm_count = ctx->sm_count;
   L.stream = s;
   return L;
