@@ -57,6 +57,9 @@ L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
 METRIC = "EM solves/s (NLEM Mpixel/s alongside) at relative residual 1e-4 (cap 300) vs FP64 oracle; % of roofline"
 
+# GPU outputs of the extra rows that the CPU-baseline leg compares with the FP64 oracle
+CROP_OUTPUTS = {}
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -72,7 +75,10 @@ def parse():
                    help="run a small profiling case (no timing output) and exit")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra rows (rho=1e-3, mixed precision, batch, learned warm start)")
-    p.add_argument("--ws-train", type=int, default=131072, help="training solves for the learned warm start")
+    p.add_argument("--ws-train", type=int, default=1000000, help="training solves for the learned warm start")
+    p.add_argument("--quick", action="store_true",
+                   help="skip the long extra rows (the batch at rho = 1, about a minute) and train the warm start "
+                        "on 131072 solves instead of --ws-train")
     return p.parse_args()
 
 
@@ -323,6 +329,71 @@ def cpu_sample_rate(seconds):
                                            f"{t_total:.1f} s of wall time on {cores} threads")
 
 
+def _bounded(run, items, seconds, chunk0=16):
+    """Run run(chunk) over successive chunks of items (growing) until `seconds` of wall time or the
+    items run out; returns (items done, seconds, outputs concatenated)."""
+    done, t, outs, chunk = 0, 0.0, [], chunk0
+    while done < len(items) and t < seconds:
+        part = items[done:done + chunk]
+        t0 = time.perf_counter()
+        outs.append(run(part))
+        t += time.perf_counter() - t0
+        done += len(part)
+        chunk *= 2
+    return done, t, (np.concatenate(outs) if outs else np.zeros(0))
+
+
+def oracle_per_config(seconds_each=3.0):
+    """The FP64 oracle (all host cores) on each workload's sample: the 64x64 workload in full
+    (sigma 20, 7x7 patches, 11x11 window, rho 1, 100 iterations), 64x64 centre crops of the
+    production (512x512, sigma 20), mixed-precision (1024x1024, 9x9 patches, 100 iterations) and
+    learned-start (2048x2048, sigma 25) images with their settings, and a seeded 4096-problem
+    subset of the standalone batch; each bounded to about `seconds_each` of wall time (the 64x64
+    workload runs in full).  The mixed-precision crop is also compared, pixel by pixel, with the GPU
+    outputs of the extra row (FP32 weights and BF16 cross terms) when that row ran."""
+    import oracle
+    import synth
+    oracle.build()
+    rows = {}
+    g1, _ = synth.noisy_image(1000, 64, 64, 20.0)
+    t0 = time.perf_counter()
+    oracle.nlem(g1, 7, 11, 200.0, 1.0, 100)
+    t1 = time.perf_counter() - t0
+    rows["64x64"] = {"pixels": 4096, "seconds": t1, "pixels_per_s": 4096 / t1}
+
+    def crop(Hc, Wc):
+        r, c = np.meshgrid(np.arange(Hc // 2 - 32, Hc // 2 + 32), np.arange(Wc // 2 - 32, Wc // 2 + 32), indexing="ij")
+        return (r * Wc + c).reshape(-1)
+    g2, _ = synth.noisy_image(SEED * 10 + 1, H, W, SIGMAS[1])
+    n, t, _ = _bounded(lambda px: oracle.nlem(g2, K_PATCH, S_WIN, 10 * SIGMAS[1], RHO, CAP, tol=TOL, check_every=CHECK,
+                                              pixels=px)["out"], crop(H, W), seconds_each)
+    rows["production_512_crop"] = {"pixels": n, "seconds": t, "pixels_per_s": n / t}
+    g3, _ = synth.noisy_image(SEED * 10 + 30, 1024, 1024, 30.0, salt_pepper=0.05)
+    px3 = crop(1024, 1024)
+    n, t, o3 = _bounded(lambda px: oracle.nlem(g3, 9, 21, 300.0, RHO, 100, pixels=px)["out"], px3, seconds_each)
+    rows["mixed_precision_1024_crop"] = {"pixels": n, "seconds": t, "pixels_per_s": n / t}
+    if "config3" in CROP_OUTPUTS and n > 0:
+        ref = o3
+        err = {}
+        for k, v in CROP_OUTPUTS["config3"].items():
+            got = v.reshape(-1)[:n].astype(np.float64)
+            e = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+            err[k] = {"max": float(e.max()), "median": float(np.median(e)), "p99": float(np.quantile(e, 0.99))}
+        rows["mixed_precision_1024_crop"]["error_vs_fp64_oracle"] = err
+    g5, _ = synth.noisy_image(SEED * 10 + 900, 2048, 2048, 25.0)
+    n, t, _ = _bounded(lambda px: oracle.nlem(g5, 7, 21, 250.0, RHO, CAP, tol=TOL, check_every=CHECK, pixels=px)["out"],
+                       crop(2048, 2048), seconds_each)
+    rows["learned_start_2048_crop"] = {"pixels": n, "seconds": t, "pixels_per_s": n / t}
+    probs = np.sort(np.random.default_rng(SEED).choice(EM_B, 4096, replace=False))
+
+    def em_chunk(pr):
+        return oracle.em_admm_batch(synth.em_points(SEED, pr, EM_N, EM_D), synth.em_weights(SEED, pr, EM_N), BOX[0],
+                                    BOX[1], RHO, CAP, tol=TOL, check_every=CHECK)[0][:, 0]
+    n, t, _ = _bounded(em_chunk, probs, seconds_each)
+    rows["standalone_4096_subset"] = {"problems": n, "seconds": t, "solves_per_s": n / t}
+    return rows
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -373,6 +444,56 @@ def extra_small_rho(nl, ctx, imgs):
             "cap_hit": float(np.mean(it >= CAP))}
 
 
+PENALTY_RHOS = (1.0, 0.1, 0.03, 0.01, 0.003, 0.001)
+
+
+def extra_penalty(nl, ctx, imgs):
+    """Per-point penalties mu_k = rho w_k (options.penalty, the penalty choice Sec. 4 leaves open)
+    against Algorithm 1's single penalty, on the production images and on 16384 standalone
+    problems, over a grid of rho; both stop at relative residual 1e-4 (in their own norms) checked
+    every 10 iterations, cap 300.  The best rho of each (fastest) is compared."""
+    import torch
+    import synth
+    rows = []
+    for pen, name in ((nl.PENALTY_UNIFORM, "uniform"), (nl.PENALTY_WEIGHTED, "weighted")):
+        for rho in PENALTY_RHOS:
+            tot_ms, its = 0.0, []
+            for i, sg in enumerate(SIGMAS):
+                ms, r = _timed(lambda: nl.nlem_denoise(imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=rho,
+                                                       iters=CAP, box=BOX, tol=TOL, check_every=CHECK, penalty=pen,
+                                                       ctx=ctx))
+                tot_ms += ms
+                its.append(r["iters_used"].reshape(-1).cpu().numpy())
+            it = np.concatenate(its)
+            rows.append({"penalty": name, "rho": rho, "mpixel_per_s": len(SIGMAS) * H * W / (tot_ms * 1e-3) / 1e6,
+                         "iters_mean": float(it.mean()), "cap_hit": float(np.mean(it >= CAP)), "ms": tot_ms})
+    best = {nm: max((r for r in rows if r["penalty"] == nm), key=lambda r: r["mpixel_per_s"])
+            for nm in ("uniform", "weighted")}
+    # standalone problems (the production batch's first 16384)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = 16384
+    pts = torch.empty((B, EM_N, EM_D), device=dev)
+    synth.device_em_points(SEED, B, EM_N, EM_D, pts.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    w = torch.from_numpy(synth.em_weights(SEED, np.arange(B), EM_N)).to(dev)
+    em_rows = []
+    for pen, name in ((nl.PENALTY_UNIFORM, "uniform"), (nl.PENALTY_WEIGHTED, "weighted")):
+        for rho in (1.0, 0.3, 0.1, 0.03, 0.01):
+            ms, r = _timed(lambda: nl.em_solve_batch(pts, w, box=BOX, rho=rho, iters=CAP, tol=TOL, check_every=CHECK,
+                                                     penalty=pen, ctx=ctx))
+            it = r["iters_used"].cpu().numpy()
+            em_rows.append({"penalty": name, "rho": rho, "solves_per_s": B / (ms * 1e-3), "iters_mean": float(it.mean()),
+                            "cap_hit": float(np.mean(it >= CAP))})
+    del pts
+    em_best = {nm: max((r for r in em_rows if r["penalty"] == nm), key=lambda r: r["solves_per_s"])
+               for nm in ("uniform", "weighted")}
+    return {"workload": "NLEM 3x512x512 (sigma 10/20/40, 7x7, 21x21, h=10 sigma) and 16384 standalone 441x49 "
+                        "problems; tol 1e-4 every 10, cap 300; uniform: pixel-pair kernel, weighted: one pixel per CTA",
+            "nlem": rows, "nlem_best": best,
+            "nlem_speedup_best_weighted_vs_best_uniform": best["weighted"]["mpixel_per_s"] / best["uniform"]["mpixel_per_s"],
+            "em": em_rows, "em_best": em_best,
+            "em_speedup_best_weighted_vs_best_uniform": em_best["weighted"]["solves_per_s"] / em_best["uniform"]["solves_per_s"]}
+
+
 def extra_mixed_precision(nl, ctx, peaks):
     """1024x1024, sigma 30 + 5% impulses, 9x9 patches, 21x21 window, h = 300, 100 iterations:
     FP32 weights against BF16 cross terms on the tensor cores, and the weight kernel alone."""
@@ -384,6 +505,11 @@ def extra_mixed_precision(nl, ctx, peaks):
     kw = dict(patch=9, window=21, h=300.0, rho=RHO, iters=100, box=BOX, ctx=ctx)
     ms32, r32 = _timed(lambda: nl.nlem_denoise(img, precision=nl.PREC_FP32, **kw))
     ms16, r16 = _timed(lambda: nl.nlem_denoise(img, precision=nl.PREC_BF16, **kw))
+    # the paper's setting (Table 1: 4 iterations), where the weight stage is a larger share
+    kw4 = dict(kw, iters=4)
+    ms32_4, _ = _timed(lambda: nl.nlem_denoise(img, precision=nl.PREC_FP32, **kw4), reps=3)
+    ms16_4, _ = _timed(lambda: nl.nlem_denoise(img, precision=nl.PREC_BF16, **kw4), reps=3)
+    ms32_0, _ = _timed(lambda: nl.nlem_denoise(img, precision=nl.PREC_FP32, **dict(kw, iters=0)), reps=3)
     table = torch.empty((Hm * Wm, 21 * 21), dtype=torch.float32, device=img.device)
     msw, _ = _timed(lambda: nl.nlem_bf16_weights(img, 9, 21, 300.0, ctx=ctx, out=table), reps=3)
     n_map = window_counts(Hm, Wm, 21)
@@ -391,9 +517,17 @@ def extra_mixed_precision(nl, ctx, peaks):
     table_bytes = float(np.sum(n_map)) * 4.0 + Hm * Wm * 4.0  # weights written + image read
     diff = (r16["out"] - r32["out"]).abs().max().item()
     del table
+    # the 64x64 centre crop of both outputs, compared with the FP64 oracle in the CPU-baseline leg
+    CROP_OUTPUTS["config3"] = {"fp32": r32["out"][480:544, 480:544].cpu().numpy(),
+                               "bf16": r16["out"][480:544, 480:544].cpu().numpy()}
     return {"workload": "1024x1024 sigma=30 + 5% impulses, k=9 (d=81), S=21, h=300, rho=1, 100 iterations",
             "fp32_mpixel_per_s": Hm * Wm / (ms32 * 1e-3) / 1e6, "bf16_mpixel_per_s": Hm * Wm / (ms16 * 1e-3) / 1e6,
             "bf16_vs_fp32_max_abs_diff": diff,
+            "four_iterations": {"fp32_mpixel_per_s": Hm * Wm / (ms32_4 * 1e-3) / 1e6,
+                                "bf16_mpixel_per_s": Hm * Wm / (ms16_4 * 1e-3) / 1e6,
+                                "fp32_setup_ms": ms32_0, "fp32_ms": ms32_4, "bf16_ms": ms16_4,
+                                "bf16_weight_kernel_share": msw / ms16_4,
+                                "fp32_setup_share": ms32_0 / ms32_4},
             "weights_kernel": {"ms": msw, "useful_tflops": useful / (msw * 1e-3) / 1e12,
                                "tensor_peak_tflops": peaks.get("bf16_tflops"),
                                "hbm_gbs": table_bytes / (msw * 1e-3) / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -401,26 +535,36 @@ def extra_mixed_precision(nl, ctx, peaks):
                                if peaks.get("hbm_gbs") else None}}
 
 
-def extra_batch(nl, ctx):
-    """64 images of uneven sizes (sides 128..1024, 22 M pixels), patch 5 or 7, window 11..21,
-    in one persistent graph-captured launch with the autotuned shape; tol 1e-4, cap 300, at
-    rho = 1e-3 (at rho = 1 nearly every pixel runs to the cap and one pass takes about a
-    minute, too long for the default run)."""
+def extra_batch(nl, ctx, with_rho1=True):
+    """64 images of uneven sizes (sides 128..1024, 22 M pixels), patch 5 or 7, window 11..21, in
+    one persistent graph-captured launch with the autotuned shape; tol 1e-4, cap 300, at rho = 1
+    (the batched workload's penalty: nearly every pixel runs to the cap, about a minute per pass;
+    skipped by --quick) and at rho = 1e-3.  The algorithmic work counts each pixel's own window
+    size and iterations."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
     specs = synth.batch_specs(SEED + 3, 64)
     ims = [torch.from_numpy(synth.noisy_image(s.seed, s.H, s.W, s.sigma)[0]).to(dev) for s in specs]
-    kw = dict(rho=1e-3, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx)
     args_ = ([s.patch for s in specs], [s.window for s in specs], [10.0 * s.sigma for s in specs])
-    outs = nl.nlem_denoise_batch(ims, *args_, **kw)          # first call: autotune + capture
-    ms, outs = _timed(lambda: nl.nlem_denoise_batch(ims, *args_, outs=outs, **kw), warm=0)
     npx = sum(s.H * s.W for s in specs)
-    its = np.concatenate([o["iters_used"].reshape(-1).cpu().numpy() for o in outs])
-    return {"workload": "64 images, sides U[128,1024], sigma {10,20,30,40}, window 11..21, patch 5/7, rho=1e-3, "
-                        "tol 1e-4 every 10, cap 300", "pixels": npx, "mpixel_per_s": npx / (ms * 1e-3) / 1e6,
-            "solves_per_s": npx / (ms * 1e-3), "iters_mean": float(its.mean()), "launch": nl.nlem_batch_config(ctx),
-            "ms": ms}
+    tf_chain, sms = nl.nlem_fp32_peak(ctx)
+    peak = sms * 128 * 2 * 2070e6 / 1e12
+    rows = {}
+    for rho in ((1.0, 1e-3) if with_rho1 else (1e-3,)):
+        kw = dict(rho=rho, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx)
+        outs = nl.nlem_denoise_batch(ims, *args_, **kw)          # first call: autotune + capture
+        ms, outs = _timed(lambda: nl.nlem_denoise_batch(ims, *args_, outs=outs, **kw), warm=0)
+        its = [o["iters_used"].cpu().numpy().astype(np.float64) for o in outs]
+        fl = sum(nlem_flops(window_counts(s.H, s.W, s.window), it, s.patch * s.patch) for s, it in zip(specs, its))
+        ita = np.concatenate([i.reshape(-1) for i in its])
+        rows[str(rho)] = {"mpixel_per_s": npx / (ms * 1e-3) / 1e6, "solves_per_s": npx / (ms * 1e-3),
+                          "iters_mean": float(ita.mean()), "cap_hit": float(np.mean(ita >= CAP)), "ms": ms,
+                          "tflops": fl / (ms * 1e-3) / 1e12, "frac": fl / (ms * 1e-3) / 1e12 / peak,
+                          "launch": nl.nlem_batch_config(ctx)}
+    return {"workload": "64 images, sides U[128,1024], sigma {10,20,30,40}, window 11..21, patch 5/7, "
+                        "tol 1e-4 every 10, cap 300", "pixels": npx, "rho": rows,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
 
 
 def extra_warm_start(nl, ctx, n_train):
@@ -433,10 +577,15 @@ def extra_warm_start(nl, ctx, n_train):
     import synth
     from paper_1501_03879_gb300 import warmstart as wst
     dev = torch.device("cuda", torch.cuda.current_device())
-    train = [(64, 20.0, 0.0), (512, 10.0, 0.0), (512, 20.0, 0.0), (512, 40.0, 0.0), (1024, 30.0, 0.05)]
+    # images drawn like the 64x64, 512x512 and impulse-noise workloads; every pixel of the small
+    # image, and an equal share of n_train from each of the others
+    train = [(64, 20.0, 0.0), (512, 10.0, 0.0), (512, 20.0, 0.0), (512, 30.0, 0.0), (512, 40.0, 0.0),
+             (1024, 30.0, 0.05), (1024, 20.0, 0.05)]
     imgs_t = [torch.from_numpy(synth.noisy_image(SEED * 10 + 500 + i, s, s, sg, salt_pepper=sp)[0]).to(dev)
               for i, (s, sg, sp) in enumerate(train)]
-    per = max(n_train // len(train), 1)
+    per = [s * s for s, _, _ in train]
+    rest = max(n_train - per[0], 0)
+    per = [per[0]] + [min(p, -(-rest // (len(train) - 1))) for p in per[1:]]
     t0 = time.perf_counter()
     feats, tgt, info = wst.make_training_set(imgs_t, [10.0 * sg for _, sg, _ in train], per_image=per, seed=1,
                                              ctx=ctx)
@@ -640,13 +789,14 @@ def run_extras(nl, ctx, imgs, args):
         pass
     out = {}
     out["rho_1e-3"] = extra_small_rho(nl, ctx, imgs)
+    out["penalty"] = extra_penalty(nl, ctx, imgs)
     out["table1"] = extra_table1(nl, ctx)
     out["convergence"] = extra_convergence(nl, ctx)
     out["color"] = extra_color(nl, ctx)
     out["sets"] = extra_sets(nl, ctx)
     out["bf16"] = extra_mixed_precision(nl, ctx, peaks)
-    out["batch"] = extra_batch(nl, ctx)
-    out["warm_start"] = extra_warm_start(nl, ctx, args.ws_train)
+    out["batch"] = extra_batch(nl, ctx, with_rho1=not args.quick)
+    out["warm_start"] = extra_warm_start(nl, ctx, 131072 if args.quick else args.ws_train)
     return out
 
 
@@ -852,7 +1002,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_sample_rate(args.cpu_seconds)
-        cpu = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "per_config": oracle_per_config()}
 
     if rank == 0:
         line = {

@@ -336,7 +336,7 @@ int nlem_selftest_timeout(nlem_ctx* ctx);
  *        H = -sum p_k ln p_k, pmax = max p_k],  p_k = w_k / sum w,
  * (inputs normalised as (v - 127.5)/64 for m and q, H / ln(nref), pmax as is) to
  *   x0 = P_C(m + 16 * y[0:d]),  rho = exp(clamp(y[d], -12, 4)).
- * Trained on solves the method itself produces (nlem_denoise_ex gives the labels) with the
+ * Trained on solves the method itself produces (nlem_ws_labels gives the labels) with the
  * library's own forward, backward and Adam kernels.  Parameter vector layout (row-major):
  *   W1 [128][2d+2], b1 [128], W2 [128][128], b2 [128], W3 [d+1][128], b3 [d+1].
  * ------------------------------------------------------------------------------------------ */
@@ -393,6 +393,24 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
                     float rho, int iters, nlem_box box, const nlem_options* opt, const int* pixels, long long npix,
                     const float* x0, const float* rho_pix, float* out, int* iters_used, float* residual,
                     float* z_out, void* stream);
+
+/* Training labels of the warm start for the listed pixels of one image (device linear indices,
+ * n of them), from solves the method itself produces (Algorithm 1 on the pixels' Sec. 3 problems,
+ * weighted-mean start, box C):
+ *   rho* = the penalty of rho_grid (host, n_rho of 1..64) that reaches relative residual tol
+ *          (checked every check_every iterations, cap `cap`) in the fewest iterations, the first
+ *          in grid order on a tie;
+ *   z*   = the solution patch of a tight solve (tight_tol, cap tight_cap) at rho*;
+ *   targets [n][d+1] (device) = [(z* - m) / 16, ln rho*], m = feats[i][0:d] (feats [n][2d+2]:
+ *          nlem_features of the same list).
+ * rho_counts (host [n_rho], nullable): how many pixels each grid penalty won (the call then waits
+ * for the device).  Entries outside [0, H*W) get NaN targets.  Workspace (about H*W*(d + 3)
+ * floats) is held by the context.  Errors: -1 for bad arguments (as nlem_denoise, or NULL
+ * arrays, a grid value that is not finite and > 0, tol or tight_tol not > 0, a cap < 1). */
+int nlem_ws_labels(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                   nlem_box box, const int* pixels, long long n, const float* rho_grid, int n_rho, float tol,
+                   int check_every, int cap, float tight_tol, int tight_cap, const float* feats, float* targets,
+                   long long* rho_counts, void* stream);
 
 /* NLEM with the learned warm start: features -> network -> EM-ADMM from (x0, rho) with the
  * stopping rule of opt (opt->tol > 0 required) and the cap iters; every pixel that reaches

@@ -45,4 +45,5 @@ from ._binding import (  # noqa: F401
     nlem_denoise_warm,
     nlem_features,
     nlem_fp32_peak,
+    nlem_ws_labels,
 )

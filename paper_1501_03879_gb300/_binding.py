@@ -109,6 +109,8 @@ def load_library():
         lib.nlem_features.argtypes = [vp, vp, i, i, i, i, i, f, vp, ll, vp, vp]
         lib.nlem_denoise_ex.argtypes = [vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, ll, vp, vp,
                                         vp, vp, vp, vp, vp]
+        lib.nlem_ws_labels.argtypes = [vp, vp, i, i, i, i, i, f, _Box, vp, ll, ctypes.POINTER(f), i, f, i, i, f, i,
+                                       vp, vp, ctypes.POINTER(ll), vp]
         lib.nlem_denoise_warm.argtypes = [vp, vp, vp, i, i, i, i, i, f, f, i, _Box, ctypes.POINTER(_Options), vp, vp,
                                           ctypes.POINTER(ll), vp]
         lib.nlem_denoise_batch_noalloc.argtypes = [ctypes.POINTER(_ImageDesc), i, f, i, _Box,
@@ -119,7 +121,7 @@ def load_library():
                      "nlem_device_status", "nlem_bf16_weights", "nlem_ws_create", "nlem_ws_destroy",
                      "nlem_ws_get_params", "nlem_ws_set_params", "nlem_ws_save", "nlem_ws_load", "nlem_ws_forward",
                      "nlem_ws_loss_grad", "nlem_ws_train_step", "nlem_ws_predict", "nlem_features", "nlem_denoise_ex",
-                     "nlem_denoise_warm"):
+                     "nlem_denoise_warm", "nlem_ws_labels"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -679,6 +681,30 @@ def nlem_features(image, patch=7, window=21, h=200.0, pixels=None, ctx: Context 
     _check(load_library().nlem_features(c.handle, ip, H, W, pitch, int(patch), int(window), float(h),
                                         _ptr(pixels), n, _ptr(feats), _stream(image.device)))
     return feats
+
+
+def nlem_ws_labels(image, pixels, feats, rho_grid, patch=7, window=21, h=200.0, box=(0.0, 255.0), tol=1e-4,
+                   check_every=5, cap=300, tight_tol=1e-6, tight_cap=2000, ctx: Context | None = None, targets=None):
+    """Warm-start training labels of the listed pixels (int32 CUDA [n]) of a float32 CUDA image,
+    computed in the library (include/nlem.h).  Returns (targets [n, d+1] CUDA, counts per grid
+    penalty as a list)."""
+    import torch
+    H, W = image.shape
+    c = ctx or _ctx(image.device)
+    n = pixels.numel()
+    d = patch * patch
+    _need(pixels, torch.int32, (n,), "pixels")
+    _need(feats, torch.float32, (n, 2 * d + 2), "feats")
+    if targets is None:
+        targets = torch.empty((n, d + 1), dtype=torch.float32, device=image.device)
+    grid = (ctypes.c_float * len(rho_grid))(*[float(r) for r in rho_grid])
+    counts = (ctypes.c_longlong * len(rho_grid))()
+    ip, pitch = _image(image)
+    _check(load_library().nlem_ws_labels(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), _Box(*box),
+                                         _ptr(pixels), n, grid, len(rho_grid), float(tol), int(check_every), int(cap),
+                                         float(tight_tol), int(tight_cap), _ptr(feats), _ptr(targets), counts,
+                                         _stream(image.device)))
+    return targets, list(counts)
 
 
 def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,

@@ -167,6 +167,14 @@ int nlem_ctx_destroy(nlem_ctx* ctx) {
   cudaFree(ctx->ws_list);
   cudaFree(ctx->ws_ulist);
   cudaFree(ctx->ws_count);
+  cudaFree(ctx->lab_out);
+  cudaFree(ctx->lab_iters);
+  cudaFree(ctx->lab_rho_map);
+  cudaFree(ctx->lab_z);
+  cudaFree(ctx->lab_best_it);
+  cudaFree(ctx->lab_best_rho);
+  cudaFree(ctx->lab_grid);
+  cudaFree(ctx->lab_counts);
   cudaFree(ctx->ws_em);
   for (int i = 0; i < 2; ++i) {
     if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);

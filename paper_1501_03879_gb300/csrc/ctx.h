@@ -60,5 +60,24 @@ struct nlem_ctx {
   long long* ws_count = nullptr;   // device element counts: [0] fallback list, [1] caller list
   size_t ws_warm_pixels = 0;
   int ws_warm_d = 0;
+  // workspace of the training labels (grown on demand): the grid solves' output and iteration
+  // images, the label penalty map, the tight solves' patches [pixel][d], the per-entry best
+  // iteration count and penalty, the penalty grid and its counts
+  float* lab_out = nullptr;
+  size_t lab_out_cap = 0;
+  int* lab_iters = nullptr;
+  size_t lab_iters_cap = 0;
+  float* lab_rho_map = nullptr;
+  size_t lab_rho_map_cap = 0;
+  float* lab_z = nullptr;
+  size_t lab_z_cap = 0;
+  int* lab_best_it = nullptr;
+  size_t lab_best_it_cap = 0;
+  float* lab_best_rho = nullptr;
+  size_t lab_best_rho_cap = 0;
+  float* lab_grid = nullptr;
+  size_t lab_grid_cap = 0;
+  unsigned long long* lab_counts = nullptr;
+  size_t lab_counts_cap = 0;
 };
 

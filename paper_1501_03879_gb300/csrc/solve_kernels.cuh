@@ -194,9 +194,18 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
     sm.pcv[i] = v;
   }
   __syncthreads();
-  // weights (same lane layout as the solver)
+  // weights (same lane layout as the solver): from the precomputed table in the mixed-precision
+  // mode (the FP32 distances are then not formed at all), else exp(-||P_i - P_j||^2 / h^2)
   float wreg[C::P];
-  {
+  if (wtab) {   // uniform over the CTA
+#pragma unroll
+    for (int p = 0; p < C::P; ++p) {
+      const int j = pg + p * C::NG;
+      const float w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;
+      wreg[p] = w;
+      if (g == 0) sm.lam[j] = (IRLS || WPEN) ? w : w * pp.inv_mu;
+    }
+  } else {
     float pc[C::Q];
     load_slice<C>(sm.pcv + g * C::QA, last, pc);
 #pragma unroll
@@ -217,8 +226,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
         }
       }
       const float Dp = point_sum<C>(D0 + D1);
-      float w = j < n ? expf(-Dp * inv_h2) : 0.f;
-      if (wtab) w = j < n ? __ldg(wtab + pix * (long long)(S * S) + j) : 0.f;   // precomputed (BF16 mode)
+      const float w = j < n ? expf(-Dp * inv_h2) : 0.f;
       wreg[p] = w;
       if (g == 0) sm.lam[j] = (IRLS || WPEN) ? w : w * pp.inv_mu;
     }

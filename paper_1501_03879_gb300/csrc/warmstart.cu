@@ -370,4 +370,102 @@ int ws_fallback_list(const int* iters_used, long long npix, int cap, int* list, 
   return (int)cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------------------------------
+// training labels: the penalty that reached the tolerance first, and the targets
+// ------------------------------------------------------------------------------------------
+__global__ void label_init_kernel(long long n, int* __restrict__ best_it, float* __restrict__ best_rho) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    best_it[i] = 0x7fffffff;
+    best_rho[i] = 1.f;
+  }
+}
+
+// after the solve with penalty rho: pixels whose iteration count beats the best so far take it
+// (strictly fewer iterations, so ties keep the earlier penalty of the grid)
+__global__ void label_select_kernel(const int* __restrict__ iters_img, long long total, const int* __restrict__ pix,
+                                    long long n, float rho, int* __restrict__ best_it, float* __restrict__ best_rho) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (pix[i] < 0 || pix[i] >= total) continue;   // outside the image: never solved
+    const int it = iters_img[pix[i]];
+    if (it < best_it[i]) {
+      best_it[i] = it;
+      best_rho[i] = rho;
+    }
+  }
+}
+
+// rho_map[pix[i]] = best_rho[i] (every other entry 1); counts[j] += #{i : best_rho[i] == grid[j]}
+__global__ void label_scatter_kernel(const int* __restrict__ pix, long long n, long long total,
+                                     const float* __restrict__ best_rho, float* __restrict__ rho_map,
+                                     const float* __restrict__ grid, int n_rho, unsigned long long* __restrict__ counts) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (pix[i] < 0 || pix[i] >= total) continue;
+    const float r = best_rho[i];
+    rho_map[pix[i]] = r;
+    for (int j = 0; j < n_rho; ++j)
+      if (grid[j] == r) {
+        atomicAdd(counts + j, 1ull);
+        break;
+      }
+  }
+}
+
+// targets[i] = [(z[pix[i]] - m_i) / kDeltaScale, ln best_rho[i]] with m_i = feats[i][0:d]; NaN for
+// list entries outside the image
+__global__ void label_targets_kernel(const float* __restrict__ z_full, long long total, const int* __restrict__ pix,
+                                     long long n, int d, const float* __restrict__ feats,
+                                     const float* __restrict__ best_rho, float* __restrict__ targets) {
+  const long long elems = n * (long long)(d + 1);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < elems;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / (d + 1);
+    const int c = (int)(e - i * (d + 1));
+    const int p = pix[i];
+    if (p < 0 || p >= total) {
+      targets[e] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    targets[e] = c < d ? (z_full[(long long)p * d + c] - feats[i * (2 * d + 2) + c]) / kDeltaScale
+                       : logf(best_rho[i]);
+  }
+}
+
+__global__ void fill_f32_kernel(float* __restrict__ p, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+namespace {
+inline int grid_for(long long work, int sm_count) {
+  long long g = (work + 255) / 256, cap = (long long)sm_count * 8;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+}  // namespace
+
+int ws_label_init(long long n, int* best_it, float* best_rho, int sm_count, cudaStream_t s) {
+  label_init_kernel<<<grid_for(n, sm_count), 256, 0, s>>>(n, best_it, best_rho);
+  return (int)cudaGetLastError();
+}
+int ws_label_select(const int* iters_img, long long total, const int* pix, long long n, float rho, int* best_it,
+                    float* best_rho, int sm_count, cudaStream_t s) {
+  label_select_kernel<<<grid_for(n, sm_count), 256, 0, s>>>(iters_img, total, pix, n, rho, best_it, best_rho);
+  return (int)cudaGetLastError();
+}
+int ws_label_scatter(const int* pix, long long n, long long total, const float* best_rho, float* rho_map,
+                     const float* grid, int n_rho, unsigned long long* counts, int sm_count, cudaStream_t s) {
+  label_scatter_kernel<<<grid_for(n, sm_count), 256, 0, s>>>(pix, n, total, best_rho, rho_map, grid, n_rho, counts);
+  return (int)cudaGetLastError();
+}
+int ws_label_targets(const float* z_full, long long total, const int* pix, long long n, int d, const float* feats,
+                     const float* best_rho, float* targets, int sm_count, cudaStream_t s) {
+  label_targets_kernel<<<grid_for(n * (d + 1), sm_count), 256, 0, s>>>(z_full, total, pix, n, d, feats, best_rho,
+                                                                       targets);
+  return (int)cudaGetLastError();
+}
+int ws_fill(float* p, long long n, float v, int sm_count, cudaStream_t s) {
+  fill_f32_kernel<<<grid_for(n, sm_count), 256, 0, s>>>(p, n, v);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace nlemk

@@ -45,5 +45,17 @@ int ws_compact_list(const int* in, long long n, long long total, int* out, long 
                     cudaStream_t s);
 int ws_fallback_list(const int* iters_used, long long npix, int cap, int* list, long long* count, int sm_count,
                      cudaStream_t s);
+// Training labels: best_it = INT_MAX, best_rho = 1; the selection after the grid solve with
+// penalty rho (iters_img is the solve's [H*W] iteration image); the scatter of the label penalties
+// into rho_map (with a count per grid value); the targets [(z* - m) / kDeltaScale, ln rho*].
+int ws_label_init(long long n, int* best_it, float* best_rho, int sm_count, cudaStream_t s);
+// List entries outside [0, total) are skipped (their targets are NaN).
+int ws_label_select(const int* iters_img, long long total, const int* pix, long long n, float rho, int* best_it,
+                    float* best_rho, int sm_count, cudaStream_t s);
+int ws_label_scatter(const int* pix, long long n, long long total, const float* best_rho, float* rho_map,
+                     const float* grid, int n_rho, unsigned long long* counts, int sm_count, cudaStream_t s);
+int ws_label_targets(const float* z_full, long long total, const int* pix, long long n, int d, const float* feats,
+                     const float* best_rho, float* targets, int sm_count, cudaStream_t s);
+int ws_fill(float* p, long long n, float v, int sm_count, cudaStream_t s);
 
 }  // namespace nlemk

@@ -444,6 +444,79 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
   return run_launch(L, "nlem_denoise_ex");
 }
 
+int nlem_ws_labels(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
+                   nlem_box box, const int* pixels, long long n, const float* rho_grid, int n_rho, float tol,
+                   int check_every, int cap, float tight_tol, int tight_cap, const float* feats, float* targets,
+                   long long* rho_counts, void* stream) {
+  int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
+  if (rc) return rc;
+  if (n < 0) return wfail(NLEM_ERR_INVALID, "n must be >= 0");
+  if (n > 0 && (!pixels || !feats || !targets)) return wfail(NLEM_ERR_INVALID, "pixels, feats and targets must be non-NULL");
+  if (!rho_grid || n_rho < 1 || n_rho > 64) return wfail(NLEM_ERR_INVALID, "rho_grid must hold 1 to 64 penalties");
+  for (int j = 0; j < n_rho; ++j)
+    if (!(rho_grid[j] > 0.f) || !std::isfinite(rho_grid[j])) return wfail(NLEM_ERR_INVALID, "penalties must be finite and > 0");
+  if (!(tol > 0.f) || !(tight_tol > 0.f) || !std::isfinite(tol) || !std::isfinite(tight_tol))
+    return wfail(NLEM_ERR_INVALID, "tol and tight_tol must be finite and > 0");
+  if (check_every < 1 || cap < 1 || tight_cap < 1) return wfail(NLEM_ERR_INVALID, "check_every, cap and tight_cap must be >= 1");
+  if (!std::isfinite(box.lo) || !std::isfinite(box.hi) || box.lo > box.hi) return wfail(NLEM_ERR_INVALID, "bad box");
+  if (rho_counts)
+    for (int j = 0; j < n_rho; ++j) rho_counts[j] = 0;
+  if (n == 0) return NLEM_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = patch * patch;
+  const size_t npix = (size_t)H * W;
+  if ((rc = grow(&ctx->lab_out, &ctx->lab_out_cap, npix, "label outputs"))) return rc;
+  if ((rc = grow(&ctx->lab_iters, &ctx->lab_iters_cap, npix, "label iterations"))) return rc;
+  if ((rc = grow(&ctx->lab_rho_map, &ctx->lab_rho_map_cap, npix, "label penalty map"))) return rc;
+  if ((rc = grow(&ctx->lab_z, &ctx->lab_z_cap, npix * d, "label patches"))) return rc;
+  if ((rc = grow(&ctx->lab_best_it, &ctx->lab_best_it_cap, (size_t)n, "label iteration counts"))) return rc;
+  if ((rc = grow(&ctx->lab_best_rho, &ctx->lab_best_rho_cap, (size_t)n, "label penalties"))) return rc;
+  if ((rc = grow(&ctx->lab_grid, &ctx->lab_grid_cap, (size_t)n_rho, "penalty grid"))) return rc;
+  if ((rc = grow(&ctx->lab_counts, &ctx->lab_counts_cap, (size_t)n_rho, "penalty counts"))) return rc;
+  cudaError_t e = cudaMemcpyAsync(ctx->lab_grid, rho_grid, sizeof(float) * n_rho, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->lab_counts, 0, sizeof(unsigned long long) * n_rho, s);
+  if (e != cudaSuccess) return wcuda(e, "label set-up");
+  const long long total = (long long)npix;
+  int ke = nlemk::ws_label_init(n, ctx->lab_best_it, ctx->lab_best_rho, ctx->sm_count, s);
+  if (ke) return wcuda((cudaError_t)ke, "label init");
+  nlem_options o;
+  nlem_options_default(&o);
+  o.tol = tol;
+  o.check_every = check_every;
+  // 1. every pixel solved with each penalty of the grid; the first to reach the tolerance wins
+  for (int j = 0; j < n_rho; ++j) {
+    rc = nlem_denoise_ex(ctx, image, H, W, pitch, patch, window, h, rho_grid[j], cap, box, &o, pixels, n, nullptr,
+                         nullptr, ctx->lab_out, ctx->lab_iters, nullptr, nullptr, stream);
+    if (rc) return rc;
+    ke = nlemk::ws_label_select(ctx->lab_iters, total, pixels, n, rho_grid[j], ctx->lab_best_it, ctx->lab_best_rho,
+                                ctx->sm_count, s);
+    if (ke) return wcuda((cudaError_t)ke, "label selection");
+  }
+  // 2. the label penalties as a per-pixel map, and how often each grid value won
+  ke = nlemk::ws_fill(ctx->lab_rho_map, total, 1.f, ctx->sm_count, s);
+  if (!ke)
+    ke = nlemk::ws_label_scatter(pixels, n, total, ctx->lab_best_rho, ctx->lab_rho_map, ctx->lab_grid, n_rho,
+                                 ctx->lab_counts, ctx->sm_count, s);
+  if (ke) return wcuda((cudaError_t)ke, "label penalty map");
+  // 3. the tight solve at each pixel's label penalty gives the label start point
+  o.tol = tight_tol;
+  rc = nlem_denoise_ex(ctx, image, H, W, pitch, patch, window, h, 1.f, tight_cap, box, &o, pixels, n, nullptr,
+                       ctx->lab_rho_map, ctx->lab_out, ctx->lab_iters, nullptr, ctx->lab_z, stream);
+  if (rc) return rc;
+  // 4. the targets of the network output
+  ke = nlemk::ws_label_targets(ctx->lab_z, total, pixels, n, d, feats, ctx->lab_best_rho, targets, ctx->sm_count, s);
+  if (ke) return wcuda((cudaError_t)ke, "label targets");
+  if (rho_counts) {
+    std::vector<unsigned long long> c((size_t)n_rho);
+    e = cudaMemcpyAsync(c.data(), ctx->lab_counts, sizeof(unsigned long long) * n_rho, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return wcuda(e, "read penalty counts");
+    for (int j = 0; j < n_rho; ++j) rho_counts[j] = (long long)c[(size_t)j];
+  }
+  return NLEM_OK;
+}
+
 int nlem_denoise_warm(nlem_ctx* ctx, nlem_warmstart* ws, const float* image, int H, int W, int pitch, int patch,
                       int window, float h, float rho_fallback, int iters, nlem_box box, const nlem_options* opt,
                       float* out, int* iters_used, long long* fallback_count, void* stream) {

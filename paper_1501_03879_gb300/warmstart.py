@@ -1,15 +1,15 @@
 """Training of the learned warm start from solves the method itself produces.
 
-For each training image, a seeded sample of pixels is solved (nlem_denoise_ex, tolerance
-1e-4) from the weighted-mean start with every penalty of a grid; the label penalty is the one
-that reaches the tolerance in the fewest iterations, and the label start point is the solution
-patch of a tight solve (tolerance 1e-6) with that penalty.  Targets for the network output y:
-y[0:d] = (z* - m) / 16 and y[d] = ln rho*.  Training runs the library's forward, backward and
-Adam kernels on shuffled minibatches (nlem_ws_train); torch only holds device arrays.
+For each training image, a seeded sample of pixels gets its features (nlem_features) and its
+labels (nlem_ws_labels): every pixel is solved (tolerance 1e-4) from the weighted-mean start with
+every penalty of a grid; the label penalty is the one that reaches the tolerance in the fewest
+iterations, and the label start point is the solution patch of a tight solve (tolerance 1e-6)
+with that penalty.  Targets for the network output y: y[0:d] = (z* - m) / 16 and y[d] = ln rho*.
+Training runs the library's forward, backward and Adam kernels on shuffled minibatches
+(nlem_ws_train).  All of it runs in the library; torch only holds device arrays and this module
+only picks the pixels.
 """
 from __future__ import annotations
-
-import math
 
 import numpy as np
 
@@ -21,40 +21,26 @@ DELTA_SCALE = 16.0
 
 def make_training_set(images, hs, patch=7, window=21, per_image=4096, seed=0, tol=1e-4, check_every=5, cap=300,
                       tight_tol=1e-6, tight_cap=2000, rho_grid=RHO_GRID, ctx=None):
-    """images: float32 CUDA tensors [H, W]; hs: their weight scales h.  Returns (feats [N,2d+2],
-    targets [N,d+1], info) on the device."""
+    """images: float32 CUDA tensors [H, W]; hs: their weight scales h; per_image: pixels sampled
+    per image (one count, or one per image).  Returns (feats [N,2d+2], targets [N,d+1], info) on
+    the device."""
     import torch
     d = patch * patch
     feats_all, tgt_all = [], []
     rng = np.random.default_rng(seed)
     best_counts = np.zeros(len(rho_grid), dtype=np.int64)
-    for img, h in zip(images, hs):
+    counts = list(per_image) if isinstance(per_image, (list, tuple)) else [per_image] * len(images)
+    for img, h, kk in zip(images, hs, counts):
         H, W = img.shape
         dev = img.device
-        k = min(per_image, H * W)
+        k = min(kk, H * W)
         pix_np = np.sort(rng.choice(H * W, k, replace=False)).astype(np.int32)
         pix = torch.from_numpy(pix_np).to(dev)
         feats = B.nlem_features(img, patch, window, h, pixels=pix, ctx=ctx)
-        best_it = torch.full((k,), 1 << 30, dtype=torch.int32, device=dev)
-        best_rho = torch.ones(k, dtype=torch.float32, device=dev)
-        pl = pix.long()
-        for rho in rho_grid:
-            r = B.nlem_denoise_ex(img, patch, window, h, rho=rho, iters=cap, tol=tol, check_every=check_every,
-                                  pixels=pix, ctx=ctx)
-            it = r["iters_used"].reshape(-1)[pl]
-            better = it < best_it
-            best_it = torch.where(better, it, best_it)
-            best_rho = torch.where(better, torch.full_like(best_rho, rho), best_rho)
-        for j, rho in enumerate(rho_grid):
-            best_counts[j] += int((best_rho == rho).sum().item())
-        rho_map = torch.ones(H * W, dtype=torch.float32, device=dev)
-        rho_map[pl] = best_rho
-        r = B.nlem_denoise_ex(img, patch, window, h, rho=1.0, iters=tight_cap, tol=tight_tol, check_every=check_every,
-                              pixels=pix, rho_pix=rho_map, z_out=True, ctx=ctx)
-        z = r["z"][pl]
-        tgt = torch.empty((k, d + 1), dtype=torch.float32, device=dev)
-        tgt[:, :d] = (z - feats[:, :d]) / DELTA_SCALE
-        tgt[:, d] = torch.log(best_rho)
+        tgt, won = B.nlem_ws_labels(img, pix, feats, rho_grid, patch=patch, window=window, h=h, tol=tol,
+                                       check_every=check_every, cap=cap, tight_tol=tight_tol, tight_cap=tight_cap,
+                                       ctx=ctx)
+        best_counts += np.asarray(won, dtype=np.int64)
         feats_all.append(feats)
         tgt_all.append(tgt)
     info = {"rho_grid": list(rho_grid), "best_rho_counts": best_counts.tolist()}

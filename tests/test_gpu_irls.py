@@ -95,10 +95,13 @@ def test_irls_bf16_weights(nl):
     r = nl.nlem_denoise(_t(g), patch=7, window=15, h=200.0, iters=4, init=1, solver=nl.SOLVER_IRLS,
                         precision=nl.PREC_BF16)
     got = r["out"].cpu().numpy().reshape(-1)
+    errs = []
     for lin in range(0, 24 * 22, 37):
         pts, w, pc = oracle.nlem_problem(g, 7, 15, 200.0, lin, weight_mode=1)
         x, _ = oracle.irls(pts, w, 0.0, 255.0, oracle.project_box(pc, 0.0, 255.0), EPS, 4)
-        assert rel_err(got[lin], x[24]) <= 1e-3
+        errs.append(float(rel_err(got[lin], x[24])))
+    print(f"IRLS on BF16 weights vs the oracle's BF16 model: max rel {max(errs):.3e}, median {np.median(errs):.3e}")
+    assert max(errs) <= TOL
 
 
 def test_irls_argument_errors(nl):

@@ -192,6 +192,47 @@ def test_pixel_list_entries_outside_the_image_are_skipped(nl):
     assert torch.all(o["iters_used"].reshape(-1).cpu()[mask] == -7)
 
 
+def test_ws_labels_match_their_definition(nl):
+    """nlem_ws_labels against its definition composed on the host from nlem_denoise_ex runs: the
+    grid penalty that reaches the tolerance first (ties to the earlier one), its win counts, and the
+    targets [(z* - m) / 16, ln rho*] from the tight solve at that penalty; an entry outside the image
+    gets NaN targets."""
+    from paper_1501_03879_gb300 import warmstart as wst
+    H, W = 40, 44
+    g, _ = synth.noisy_image(8150, H, W, 25.0)
+    img = torch.from_numpy(g).to(DEV)
+    rng = np.random.default_rng(3)
+    pix_np = np.sort(rng.choice(H * W, 300, replace=False)).astype(np.int32)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    feats = nl.nlem_features(img, 7, 21, 250.0, pixels=pix)
+    grid = (1e-3, 1e-2, 0.1, 1.0)
+    tgt, counts = nl.nlem_ws_labels(img, pix, feats, grid, h=250.0, tol=1e-4, check_every=5, cap=300,
+                                    tight_tol=1e-6, tight_cap=1000)
+    its = []
+    for rho in grid:
+        r = nl.nlem_denoise_ex(img, 7, 21, 250.0, rho=rho, iters=300, tol=1e-4, check_every=5, pixels=pix)
+        its.append(r["iters_used"].reshape(-1).cpu().numpy()[pix_np])
+    its = np.stack(its)                              # [grid, n]
+    best = np.argmin(its, axis=0)                    # first minimum: the earlier penalty on ties
+    rho_star = np.asarray(grid, dtype=np.float32)[best]
+    assert counts == [int(np.sum(best == j)) for j in range(len(grid))]
+    rho_map = np.ones(H * W, dtype=np.float32)
+    rho_map[pix_np] = rho_star
+    r = nl.nlem_denoise_ex(img, 7, 21, 250.0, rho=1.0, iters=1000, tol=1e-6, check_every=5, pixels=pix,
+                           rho_pix=torch.from_numpy(rho_map).to(DEV), z_out=True)
+    z = r["z"].cpu().numpy()[pix_np]
+    m = feats.cpu().numpy()[:, :49]
+    got = tgt.cpu().numpy()
+    assert np.allclose(got[:, :49], (z - m) / wst.DELTA_SCALE, rtol=0, atol=1e-6)
+    assert np.allclose(got[:, 49], np.log(rho_star.astype(np.float64)), rtol=0, atol=1e-6)
+    # an index outside the image
+    bad = torch.tensor([5, H * W + 3], dtype=torch.int32, device=DEV)
+    fb = nl.nlem_features(img, 7, 21, 250.0, pixels=bad)
+    tb, cb = nl.nlem_ws_labels(img, bad, fb, grid, h=250.0, tight_cap=50)
+    tb = tb.cpu().numpy()
+    assert np.all(np.isfinite(tb[0])) and np.all(np.isnan(tb[1])) and sum(cb) == 1
+
+
 def test_trained_warm_start_gains_over_plain_admm(nl):
     """Train on solves of two synthetic images, evaluate on a held-out one: the learned start and
     penalty reach the 1e-4 residual in far fewer iterations than plain EM-ADMM (rho = 1) and
@@ -211,8 +252,8 @@ def test_trained_warm_start_gains_over_plain_admm(nl):
     it_best = float(plain_best["iters_used"].float().mean().item())
     n = 64 * 64
     warm_work = ev["warm_iters"] + 300.0 * ev["fallback"] / n
-    print(f"warm {ev['warm_iters']:.1f} it (+{ev['fallback']} fallbacks), plain rho=1 {ev['plain_iters']:.1f}, "
-          f"plain rho={best_rho} {it_best:.1f}")
+    print(f"warm {ev['warm_iters']:.1f} it (+{ev['fallback']} fallbacks, work {warm_work:.2f}), plain rho=1 "
+          f"{ev['plain_iters']:.1f}, plain rho={best_rho} {it_best:.1f}")
     assert warm_work < 0.25 * ev["plain_iters"]
     assert warm_work <= 1.25 * it_best
     assert ev["fallback"] <= 0.05 * n
