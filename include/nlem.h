@@ -275,6 +275,16 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
 int nlem_batch_config(nlem_ctx* ctx, char* buf, int len);
 
 /*
+ * nlem_batch_force_config - pins the launch shape of the context's next nlem_denoise_batch calls
+ * instead of the autotuner's choice (variant -1 restores the autotuner).  variant 0: one solver
+ * shape per patch size (448 point slots for 7x7 patches, 512 for 5x5); variant 1: a shape per
+ * window-size class (7x7: 128, 256 or 448 slots; 5x5: 256 or 512), so that small windows do not
+ * iterate over empty slots.  fetch >= 1 work items per queue access, 1 or 2 CTAs per SM.  Drops the
+ * captured graph.  Errors: -1 for a NULL ctx or values out of range.
+ */
+int nlem_batch_force_config(nlem_ctx* ctx, int variant, int fetch, int ctas_per_sm);
+
+/*
  * nlem_denoise_batch_noalloc - nlem_denoise_batch for callers that cannot allocate device
  * memory: code that runs inside another framework's allocator or memory pool, or under a
  * memory budget in which every device allocation belongs to the host application, and so may

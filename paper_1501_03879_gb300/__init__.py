@@ -33,6 +33,7 @@ from ._binding import (  # noqa: F401
     lib_path,
     load_library,
     nlem_batch_config,
+    nlem_batch_force_config,
     nlem_bf16_weights,
     nlem_denoise,
     nlem_denoise_batch,

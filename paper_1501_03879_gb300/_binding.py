@@ -90,6 +90,7 @@ def load_library():
         lib.nlem_fp32_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
+        lib.nlem_batch_force_config.argtypes = [vp, i, i, i]
         lib.nlem_device_status.argtypes = [vp]
         lib.nlem_selftest_timeout.argtypes = [vp]
         lib.nlem_bf16_weights.argtypes = [vp, vp, i, i, i, i, i, f, vp, vp]
@@ -117,7 +118,7 @@ def load_library():
                                                    ctypes.POINTER(_Options), vp]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "em_solve_batch_host",
                      "nlem_denoise",
-                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_denoise_batch_noalloc",
+                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_batch_force_config", "nlem_denoise_batch_noalloc",
                      "nlem_device_status", "nlem_bf16_weights", "nlem_ws_create", "nlem_ws_destroy",
                      "nlem_ws_get_params", "nlem_ws_set_params", "nlem_ws_save", "nlem_ws_load", "nlem_ws_forward",
                      "nlem_ws_loss_grad", "nlem_ws_train_step", "nlem_ws_predict", "nlem_features", "nlem_denoise_ex",
@@ -548,6 +549,14 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
         _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box),
                                                          ctypes.byref(o), _stream(dev)))
     return outs
+
+
+def nlem_batch_force_config(variant, fetch=1, ctas_per_sm=2, ctx: Context | None = None):
+    """Pin the batched launch's shape (variant 0 or 1, see include/nlem.h); variant -1 restores
+    the autotuner."""
+    import torch
+    c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
+    _check(load_library().nlem_batch_force_config(c.handle, int(variant), int(fetch), int(ctas_per_sm)))
 
 
 def nlem_device_status(ctx: Context | None = None) -> int:

@@ -801,8 +801,12 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
     std::snprintf(key, sizeof(key), "sm%d/patches%d/S%d/tol%d/it%d/init%d", ctx->sm_count, mask, maxS,
                   prm.tol > 0.f ? 1 : 0, iters, init_mode);
     nlemk::BatchConfig cfg{};
-    rc = autotune_batch(ctx, L, key, s, &cfg);
-    if (rc) return rc;
+    if (ctx->forced.variant >= 0) {
+      cfg = ctx->forced;
+    } else {
+      rc = autotune_batch(ctx, L, key, s, &cfg);
+      if (rc) return rc;
+    }
     // capture queue reset + launch once on the private stream, after the upload completes
     L.cfg = cfg;
     L.stride = 1;
@@ -838,6 +842,22 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
   }
   cudaError_t e = cudaGraphLaunch(ctx->plan.exec, s);
   if (e != cudaSuccess) return cuda_fail(e, "launch batch graph");
+  return NLEM_OK;
+}
+
+int nlem_batch_force_config(nlem_ctx* ctx, int variant, int fetch, int ctas_per_sm) {
+  if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
+  if (variant < 0) {
+    ctx->forced = nlemk::BatchConfig{-1, 0, 0};
+  } else {
+    if (variant >= nlemk::kBatchVariants) return fail(NLEM_ERR_INVALID, "variant must be < %d", nlemk::kBatchVariants);
+    if (fetch < 1 || ctas_per_sm < 1 || ctas_per_sm > 2)
+      return fail(NLEM_ERR_INVALID, "fetch >= 1 and 1 <= ctas_per_sm <= 2 are required");
+    ctx->forced = nlemk::BatchConfig{variant, fetch, ctas_per_sm};
+  }
+  // the next call captures a new graph with this shape
+  if (ctx->have_plan && ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
+  ctx->have_plan = false;
   return NLEM_OK;
 }
 

@@ -1,8 +1,8 @@
 // Batched NLEM over images of uneven sizes in ONE persistent launch (Sec. 3 applied to many
 // images at once): every (image, pixel) pair is a work item; CTAs take items from a device
 // work queue (one atomic counter in the context workspace) until the queue is empty.  Images
-// with 5x5 and 7x7 patches share the launch: the CTA solves each item with the kernel shape
-// compiled for that patch size.  The host side captures queue reset + launch in a CUDA graph
+// with 5x5 and 7x7 patches share the launch: the CTA solves each item with a kernel shape
+// compiled for that patch size (one per patch size, or one per window-size class).  The host side captures queue reset + launch in a CUDA graph
 // and picks the launch shape with a small autotuner.
 #include <cuda_runtime.h>
 
@@ -19,14 +19,19 @@ namespace nlemk {
 
 namespace {
 
-template <class CA, int KA, class CB, int KB>
+// The solver shape of an item: CA (patch KA) or CB (patch KB) for the largest windows, and with
+// SIZED the shapes of fewer point slots for smaller windows (CA1 / CA2 up to their capacities for
+// patch KA, CB1 for patch KB), so that a small window does not iterate over empty slots.  All
+// shapes use the same CTA size; their shared-memory carves alias one buffer (one item at a time).
+template <class CA, int KA, class CB, int KB, bool SIZED = false, class CA1 = CA, class CA2 = CA, class CB1 = CB>
 __global__ void __launch_bounds__(CA::NT, 2)
 nlem_batch_kernel(const BatchImage* __restrict__ imgs, int count, long long total, long long stride,
                   unsigned long long* __restrict__ queue, int fetch, SolveParams prm, int init_mode) {
-  static_assert(CA::NT == CB::NT, "both shapes must use the same CTA size");
+  static_assert(CA::NT == CB::NT && CA1::NT == CA::NT && CA2::NT == CA::NT && CB1::NT == CB::NT,
+                "every shape must use the same CTA size");
   extern __shared__ float4 smem_raw[];
-  Smem<CA> smA(reinterpret_cast<float*>(smem_raw));   // the two carves share the buffer:
-  Smem<CB> smB(reinterpret_cast<float*>(smem_raw));   // one item is solved at a time
+  Smem<CA> smA(reinterpret_cast<float*>(smem_raw));
+  Smem<CB> smB(reinterpret_cast<float*>(smem_raw));
   __shared__ long long s_base;
   for (;;) {
     if (threadIdx.x == 0) s_base = (long long)atomicAdd(queue, (unsigned long long)fetch);
@@ -44,21 +49,39 @@ nlem_batch_kernel(const BatchImage* __restrict__ imgs, int count, long long tota
       }
       const BatchImage& im = imgs[lo];
       const long long pix = item - im.pix_begin;
+      const int nmax = im.S * im.S;
       if (im.patch == KA) {
-        nlem_pixel<CA, KA>(smA, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
-                           im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        if (SIZED && nmax <= CA1::CAP) {
+          Smem<CA1> sm1(reinterpret_cast<float*>(smem_raw));
+          nlem_pixel<CA1, KA>(sm1, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix,
+                              im.out, im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        } else if (SIZED && nmax <= CA2::CAP) {
+          Smem<CA2> sm2(reinterpret_cast<float*>(smem_raw));
+          nlem_pixel<CA2, KA>(sm2, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix,
+                              im.out, im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        } else {
+          nlem_pixel<CA, KA>(smA, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
+                             im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        }
       } else {
-        nlem_pixel<CB, KB>(smB, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
-                           im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        if (SIZED && nmax <= CB1::CAP) {
+          Smem<CB1> sm1(reinterpret_cast<float*>(smem_raw));
+          nlem_pixel<CB1, KB>(sm1, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix,
+                              im.out, im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        } else {
+          nlem_pixel<CB, KB>(smB, im.img, im.H, im.W, im.pitch, im.S, im.inv_h2, im.ih2, prm, init_mode, pix, im.out,
+                             im.iters, im.resid, nullptr, nullptr, nullptr, PixelExtra{});
+        }
       }
     }
   }
 }
 
-template <class CA, int KA, class CB, int KB>
+template <class CA, int KA, class CB, int KB, bool SIZED = false, class CA1 = CA, class CA2 = CA, class CB1 = CB>
 int launch_variant(const BatchLaunch& L) {
-  auto kern = nlem_batch_kernel<CA, KA, CB, KB>;
-  const size_t smem = std::max(CA::SMEM_BYTES, CB::SMEM_BYTES);
+  auto kern = nlem_batch_kernel<CA, KA, CB, KB, SIZED, CA1, CA2, CB1>;
+  const size_t smem = std::max(std::max(CA::SMEM_BYTES, CB::SMEM_BYTES),
+                               std::max(std::max(CA1::SMEM_BYTES, CA2::SMEM_BYTES), CB1::SMEM_BYTES));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const long long items = (L.total + L.stride - 1) / L.stride;
@@ -74,8 +97,9 @@ int launch_variant(const BatchLaunch& L) {
 }  // namespace
 
 int batch_max_points(int patch, int variant) {
+  (void)variant;   // both variants hold the largest windows in the same shapes
   if (patch == 7) return E49_7::CAP;
-  if (patch == 5) return variant == 0 ? E25_4::CAP : E25_7::CAP;
+  if (patch == 5) return E25_4::CAP;
   return 0;
 }
 
@@ -89,7 +113,7 @@ int batch_tile_fits(int patch, int window) {
 int launch_batch(const BatchLaunch& L) {
   switch (L.cfg.variant) {
     case 0: return launch_variant<E49_7, 7, E25_4, 5>(L);
-    case 1: return launch_variant<E49_7, 7, E25_7, 5>(L);
+    case 1: return launch_variant<E49_7, 7, E25_4, 5, true, E49_2, E49_4x3, E25_2>(L);
     default: return -1;
   }
 }
@@ -97,7 +121,7 @@ int launch_batch(const BatchLaunch& L) {
 const char* batch_variant_name(int v) {
   switch (v) {
     case 0: return "d49:G2xQ25xP7/128thr + d25:G1xQ25xP4/128thr";
-    case 1: return "d49:G2xQ25xP7/128thr + d25:G1xQ25xP7/128thr";
+    case 1: return "by window: d49 P2 (n<=128) / P4 (n<=256) / P7 + d25 P2 (n<=256) / P4, 128thr";
     default: return "?";
   }
 }

@@ -46,6 +46,7 @@ struct nlem_ctx {
   unsigned long long* ws_queue = nullptr;
   cudaStream_t cap_stream = nullptr;                // private stream used for graph capture
   std::map<std::string, nlemk::BatchConfig> tune;   // autotuner results by workload class
+  nlemk::BatchConfig forced{-1, 0, 0};              // a launch shape set by nlem_batch_force_config
   BatchPlan plan;
   bool have_plan = false;
   std::string last_cfg;

@@ -34,16 +34,23 @@ def _specs():
             (31, 33, 20.0, 7, 15), (12, 45, 10.0, 5, 9), (41, 41, 30.0, 5, 17)]
 
 
-def test_batch_matches_oracle_every_pixel(nl):
+@pytest.mark.parametrize("forced", [None, 0, 1])
+def test_batch_matches_oracle_every_pixel(nl, forced):
+    """Every pixel of seven uneven images against the oracle, with the autotuner's launch shape and
+    with each shape variant pinned (one solver shape per patch size; one per window-size class)."""
     specs = _specs()
     imgs_h = [synth.noisy_image(3000 + i, H, W, s)[0] for i, (H, W, s, k, S) in enumerate(specs)]
     imgs = [torch.from_numpy(g).to(DEV) for g in imgs_h]
     ctx = nl.Context(0)
+    if forced is not None:
+        nl.nlem_batch_force_config(forced, fetch=4, ctas_per_sm=2, ctx=ctx)
     T = 25
     outs = nl.nlem_denoise_batch(imgs, [k for *_, k, S in specs], [S for *_, S in specs],
                                  [10 * s for _, _, s, _, _ in specs], rho=0.7, iters=T, ctx=ctx)
     cfg = nl.nlem_batch_config(ctx)
     assert "CTA/SM" in cfg
+    if forced == 1:
+        assert cfg.startswith("by window")
     for i, ((H, W, s, k, S), g) in enumerate(zip(specs, imgs_h)):
         ref = oracle.nlem(g, k, S, 10 * s, 0.7, T)
         err = rel_err(outs[i]["out"].cpu().numpy(), ref["out"])
