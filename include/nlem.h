@@ -433,6 +433,18 @@ int nlem_denoise_warm(nlem_ctx* ctx, nlem_warmstart* ws, const float* image, int
                       float* out, int* iters_used, long long* fallback_count, void* stream);
 
 /*
+ * nlem_debug_status - the bounds-check record of the debug build (libnlem_debug.so, built with
+ * -DNLEM_DEBUG): every shared-memory tile, point-row and image index that depends on the image
+ * size, window clipping, reflect padding or work-item lookup is checked against what it indexes;
+ * an index outside it is recorded and the access skipped (a load reads 0).  Waits for the device,
+ * then reports the first fault (site: the nlemk::DebugSite of csrc/debug.h, index, limit) and
+ * the number of faults since the last reset (0 = none); reset != 0 clears the record.  A tool for
+ * development (the sanitizer's stand-in), not part of the method.  Returns -5 in the release
+ * build (no checks compiled; outputs 0).
+ */
+int nlem_debug_status(int reset, int* site, long long* index, long long* limit, long long* count);
+
+/*
  * nlem_fp32_peak - measured FP32 FMA throughput of the current device (TFLOP/s, counting an
  * FMA as 2 flops), from a register-only FMA-chain kernel timed with CUDA events; also
  * returns the SM count.  Used as the roofline denominator of the ALU-bound kernels.

@@ -41,6 +41,7 @@ from ._binding import (  # noqa: F401
     nlem_denoise_color,
     nlem_denoise_ex,
     nlem_denoise_host,
+    nlem_debug_status,
     nlem_device_status,
     nlem_selftest_timeout,
     nlem_denoise_warm,

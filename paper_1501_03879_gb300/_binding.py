@@ -91,6 +91,8 @@ def load_library():
         lib.nlem_denoise_batch.argtypes = [vp, ctypes.POINTER(_ImageDesc), i, f, i, _Box, ctypes.POINTER(_Options), vp]
         lib.nlem_batch_config.argtypes = [vp, ctypes.c_char_p, i]
         lib.nlem_batch_force_config.argtypes = [vp, i, i, i]
+        lib.nlem_debug_status.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(ll), ctypes.POINTER(ll),
+                                          ctypes.POINTER(ll)]
         lib.nlem_device_status.argtypes = [vp]
         lib.nlem_selftest_timeout.argtypes = [vp]
         lib.nlem_bf16_weights.argtypes = [vp, vp, i, i, i, i, i, f, vp, vp]
@@ -118,7 +120,7 @@ def load_library():
                                                    ctypes.POINTER(_Options), vp]
         for name in ("nlem_ctx_create", "nlem_ctx_destroy", "em_solve", "em_solve_batch", "em_solve_batch_host",
                      "nlem_denoise",
-                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_batch_force_config", "nlem_denoise_batch_noalloc",
+                     "nlem_denoise_host", "nlem_fp32_peak", "nlem_denoise_batch", "nlem_batch_config", "nlem_batch_force_config", "nlem_debug_status", "nlem_denoise_batch_noalloc",
                      "nlem_device_status", "nlem_bf16_weights", "nlem_ws_create", "nlem_ws_destroy",
                      "nlem_ws_get_params", "nlem_ws_set_params", "nlem_ws_save", "nlem_ws_load", "nlem_ws_forward",
                      "nlem_ws_loss_grad", "nlem_ws_train_step", "nlem_ws_predict", "nlem_features", "nlem_denoise_ex",
@@ -557,6 +559,15 @@ def nlem_batch_force_config(variant, fetch=1, ctas_per_sm=2, ctx: Context | None
     import torch
     c = ctx or _ctx(torch.device("cuda", torch.cuda.current_device()))
     _check(load_library().nlem_batch_force_config(c.handle, int(variant), int(fetch), int(ctas_per_sm)))
+
+
+def nlem_debug_status(reset=True):
+    """The debug build's bounds-check record (include/nlem.h): dict(count, site, index, limit);
+    raises NlemError (-5) in the release build."""
+    site, idx, lim, cnt = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().nlem_debug_status(1 if reset else 0, ctypes.byref(site), ctypes.byref(idx), ctypes.byref(lim),
+                                            ctypes.byref(cnt)))
+    return dict(count=cnt.value, site=site.value, index=idx.value, limit=lim.value)
 
 
 def nlem_device_status(ctx: Context | None = None) -> int:

@@ -1,5 +1,7 @@
 """Build libnlem.so (sm_103a) in-tree with nvcc: one object per translation unit, compiled in
-parallel, then linked into paper_1501_03879_gb300/lib/libnlem.so."""
+parallel, then linked into paper_1501_03879_gb300/lib/libnlem.so.  build(debug=True) builds the
+same sources with -DNLEM_DEBUG (the bounds checks of csrc/debug.h; relocatable device code, so that
+every translation unit records into one device record) into lib/libnlem_debug.so."""
 from __future__ import annotations
 
 import os
@@ -11,8 +13,11 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build", "obj")
+OBJ_DEBUG = os.path.join(ROOT, "_build", "obj_debug")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libnlem.so")
+LIB_DEBUG = os.path.join(LIBDIR, "libnlem_debug.so")
+DEBUG_FLAGS = ["-DNLEM_DEBUG", "-rdc=true"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -35,17 +40,19 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    objdir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
+    extra = DEBUG_FLAGS if debug else []
+    os.makedirs(objdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     hdrs = headers()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            cmd = ["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = ["nvcc", *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)
@@ -66,13 +73,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 failed.append(cmd[-3])
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(failed))
-    if force or jobs or _stale(LIB, objs):
-        cmd = ["nvcc", *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    if force or jobs or _stale(lib, objs):
+        cmd = ["nvcc", *ARCH, *(["-rdc=true"] if debug else []), "-shared", "-o", lib, *objs, "-lcudart"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
+    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv, debug="--debug" in sys.argv)

@@ -15,6 +15,7 @@
 #include "../../include/nlem.h"
 #include "batch.h"
 #include "kernels.h"
+#include "trace.h"
 
 #include "ctx.h"
 
@@ -190,6 +191,7 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
                    nlem_box box, float rho, int iters, const float* x0, const nlem_options* opt,
                    float* x_out, int* iters_used, float* residual, double* obj64, double* kkt64,
                    void* stream) {
+  NLEM_TRACE("em_solve_batch");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "em_solve_batch"))) return rc;
@@ -230,6 +232,7 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
 int em_solve_batch_set(nlem_ctx* ctx, const float* points, const float* weights, long long B, int n, int d,
                        const nlem_set* set, float rho, int iters, const float* x0, const nlem_options* opt,
                        float* x_out, int* iters_used, float* residual, void* stream) {
+  NLEM_TRACE("em_solve_batch_set");
   const nlem_box any = {0.f, 0.f};
   int rc = check_common(ctx, any, rho, iters, opt);
   if (rc) return rc;
@@ -280,6 +283,7 @@ int em_solve_batch_set(nlem_ctx* ctx, const float* points, const float* weights,
 
 int em_solve(nlem_ctx* ctx, const float* points, const float* weights, int n, int d, nlem_box box, float rho,
              int iters, float* x_out, void* stream) {
+  NLEM_TRACE("em_solve");
   return em_solve_batch(ctx, points, weights, 1, n, d, box, rho, iters, nullptr, nullptr, x_out, nullptr, nullptr,
                         nullptr, nullptr, stream);
 }
@@ -288,6 +292,7 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
                         int d, nlem_box box, float rho, int iters, const float* x0_host, const nlem_options* opt,
                         long long chunk, float* x_out_host, int* iters_used_host, float* residual_host,
                         void* stream) {
+  NLEM_TRACE("em_solve_batch_host");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "em_solve_batch_host"))) return rc;
@@ -381,6 +386,7 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
 int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
                  float rho, int iters, nlem_box box, const nlem_options* opt, float* out, int* iters_used,
                  float* residual, double* obj64, double* kkt64, void* stream) {
+  NLEM_TRACE("nlem_denoise");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1 (got %dx%d)", H, W);
@@ -465,6 +471,7 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
 int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int channels, int patch,
                        int window, float h, float rho, int iters, nlem_box box, const nlem_options* opt, float* out,
                        int* iters_used, float* residual, double* obj64, double* kkt64, void* stream) {
+  NLEM_TRACE("nlem_denoise_color");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "nlem_denoise_color"))) return rc;
@@ -522,6 +529,7 @@ int nlem_denoise_color(nlem_ctx* ctx, const float* image, int H, int W, int pitc
 int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int patch, int window, float h,
                       float rho, int iters, nlem_box box, const nlem_options* opt, float* out_host,
                       int* iters_used_host, void* stream) {
+  NLEM_TRACE("nlem_denoise_host");
   if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
   if (!image_host || !out_host) return fail(NLEM_ERR_INVALID, "image_host and out_host must be non-NULL");
   if (H < 1 || W < 1) return fail(NLEM_ERR_INVALID, "image must be at least 1x1");
@@ -561,6 +569,7 @@ int nlem_denoise_host(nlem_ctx* ctx, const float* image_host, int H, int W, int 
 
 int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
                       float* wtab, void* stream) {
+  NLEM_TRACE("nlem_bf16_weights");
   if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
   if (!image || !wtab) return fail(NLEM_ERR_INVALID, "image and wtab must be non-NULL");
   if (H < 1 || W < 1 || pitch < W) return fail(NLEM_ERR_INVALID, "bad image size or pitch");
@@ -585,6 +594,7 @@ int nlem_bf16_weights(nlem_ctx* ctx, const float* image, int H, int W, int pitch
 }
 
 int nlem_device_status(nlem_ctx* ctx) {
+  NLEM_TRACE("nlem_device_status");
   if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
   int rc = set_device(ctx);
   if (rc) return rc;
@@ -602,6 +612,7 @@ int nlem_device_status(nlem_ctx* ctx) {
 }
 
 int nlem_selftest_timeout(nlem_ctx* ctx) {
+  NLEM_TRACE("nlem_selftest_timeout");
   if (!ctx) return fail(NLEM_ERR_INVALID, "ctx is NULL");
   int rc = set_device(ctx);
   if (rc) return rc;
@@ -633,6 +644,7 @@ int nlem_selftest_timeout(nlem_ctx* ctx) {
 }
 
 int nlem_fp32_peak(nlem_ctx* ctx, double* tflops, int* sm_count) {
+  NLEM_TRACE("nlem_fp32_peak");
   if (!ctx || !tflops) return fail(NLEM_ERR_INVALID, "ctx and tflops must be non-NULL");
   int rc = set_device(ctx);
   if (rc) return rc;
@@ -709,6 +721,7 @@ extern "C" {
 
 int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, float rho, int iters, nlem_box box,
                        const nlem_options* opt, void* stream) {
+  NLEM_TRACE("nlem_denoise_batch");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
   if ((rc = admm_only(opt, "nlem_denoise_batch"))) return rc;

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "batch.h"
+#include "debug.h"
 #include "shapes.h"
 #include "solve_kernels.cuh"
 
@@ -49,6 +50,7 @@ nlem_batch_kernel(const BatchImage* __restrict__ imgs, int count, long long tota
       }
       const BatchImage& im = imgs[lo];
       const long long pix = item - im.pix_begin;
+      if (!NLEM_DBG_OK(pix, (long long)im.H * im.W, kDbgBatchItem)) continue;
       const int nmax = im.S * im.S;
       if (im.patch == KA) {
         if (SIZED && nmax <= CA1::CAP) {

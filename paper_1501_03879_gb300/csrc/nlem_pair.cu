@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "debug.h"
 #include "kernels.h"
 #include "solver_common.cuh"
 
@@ -571,8 +572,12 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
   const int nA = nwr * (a1 - a0 + 1), nB = hasB ? nwr * (b1 - b0 + 1) : 0;
   const int TC = (b1 - a0 + 1) + 2 * HK, TR = nwr + 2 * HK;
   for (int tr = warp; tr < TR; tr += NW) {
-    const float* grow = img + (size_t)reflect(r0 - HK + tr, H) * pitch;
-    for (int tc = lane; tc < TC; tc += 32) sm.tile[tr * TC + tc] = __ldg(grow + reflect(a0 - HK + tc, W));
+    const long long gr = (long long)reflect(r0 - HK + tr, H) * pitch;
+    for (int tc = lane; tc < TC; tc += 32) {
+      const long long gi = gr + reflect(a0 - HK + tc, W);
+      const float v = NLEM_DBG_OK(gi, (long long)H * pitch, kDbgImageRead) ? __ldg(img + gi) : 0.f;
+      if (NLEM_DBG_OK(tr * TC + tc, TILE_MAX, kDbgPairTile)) sm.tile[tr * TC + tc] = v;
+    }
   }
   if (t == 0) {
     sm.scal[0] = 0.f;
@@ -617,9 +622,11 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int q = 4 * i4 + c;
-        v[c] = (u >= 0 && q < D) ? tp[(q / K) * TC + (q % K)] : 0.f;
+        const int ti = r * TC + (u - a0) + (q / K) * TC + (q % K);
+        v[c] = (u >= 0 && q < D && NLEM_DBG_OK(ti, TR * TC, kDbgPairTile)) ? tp[(q / K) * TC + (q % K)] : 0.f;
       }
-      row4[i4] = make_float4(v[0], v[1], v[2], v[3]);
+      if (NLEM_DBG_OK(dst - sm.pts + 4 * i4 + 3, OFF_LAM - OFF_PTS, kDbgPairRow))
+        row4[i4] = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
   // centre patches in the column layout (slots that hold no coordinate are zero)
@@ -627,7 +634,8 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
     const int col = i >> 2, slot = i & 3, sg = col >> 3, c = col & 7, X = c >> 2, cc = c & 3;
     const int q = cc < 3 ? sg * QM + 4 * cc + slot : ((sg == G - 1 && slot == 0) ? 4 * G * NQ : -1);
     float v = 0.f;
-    if (q >= 0 && (X == 0 || hasB)) v = sm.tile[(y - r0 + q / K) * TC + (x + X - a0 + q % K)];
+    const int ti = (y - r0 + q / K) * TC + (x + X - a0 + q % K);
+    if (q >= 0 && (X == 0 || hasB) && NLEM_DBG_OK(ti, TR * TC, kDbgPairTile)) v = sm.tile[ti];
     sm.pcv[vcol(col) * 4 + slot] = v;
   }
   __syncthreads();

@@ -14,6 +14,7 @@
 #include "../../include/nlem.h"
 #include "batch.h"
 #include "kernels.h"
+#include "trace.h"
 
 namespace {
 
@@ -38,6 +39,7 @@ int nerr(int code, const char* msg, int image = -1) {
 
 extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int count, float rho, int iters,
                                           nlem_box box, const nlem_options* opt, void* stream) {
+  NLEM_TRACE("nlem_denoise_batch_noalloc");
   if (count < 0 || count > NLEM_NOALLOC_MAX_IMAGES)
     return nerr(NLEM_ERR_INVALID, "count must be in [0, NLEM_NOALLOC_MAX_IMAGES]");
   if (count == 0) return NLEM_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "admm_core.cuh"
+#include "debug.h"
 #include "irls_core.cuh"
 #include "kernels.h"
 
@@ -43,7 +44,8 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       const int sg = q / C::Q, i = q - sg * C::Q;
       const float v = __ldg(P + idx);
       bad |= !isfinite(v);
-      sm.pts[j * C::DP + sg * C::QA + i] = v;
+      const int r = j * C::DP + sg * C::QA + i;
+      if (NLEM_DBG_OK(r, C::SZ_PTS, kDbgPointRow)) sm.pts[r] = v;
     }
     for (int j = t; j < C::CAP; j += C::NT) {
       float lam = 0.f;
@@ -155,8 +157,12 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   {
     const int lane = t & 31, warp = t >> 5;
     for (int tr = warp; tr < TR; tr += C::NW) {
-      const float* grow = img + (size_t)reflect_idx(r0 - HK + tr, H) * pitch;
-      for (int tc = lane; tc < TC; tc += 32) sm.tile[tr * TC + tc] = __ldg(grow + reflect_idx(c0 - HK + tc, W));
+      const long long gr = (long long)reflect_idx(r0 - HK + tr, H) * pitch;
+      for (int tc = lane; tc < TC; tc += 32) {
+        const long long gi = gr + reflect_idx(c0 - HK + tc, W);
+        const float v = NLEM_DBG_OK(gi, (long long)H * pitch, kDbgImageRead) ? __ldg(img + gi) : 0.f;
+        if (NLEM_DBG_OK(tr * TC + tc, C::SZ_WRED, kDbgTileWrite)) sm.tile[tr * TC + tc] = v;
+      }
     }
   }
   for (int i = n * C::DP + t; i < C::CAP * C::DP; i += C::NT) sm.pts[i] = 0.f;
@@ -176,9 +182,11 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int slot = 4 * i4 + c, q = sg * C::Q + slot;
-          v[c] = (slot < C::Q && q < C::D) ? tp[(q / K) * TC + (q % K)] : 0.f;
+          const int ti = (jr + q / K) * TC + jc + (q % K);
+          v[c] = (slot < C::Q && q < C::D && NLEM_DBG_OK(ti, TR * TC, kDbgTileRead)) ? tp[(q / K) * TC + (q % K)] : 0.f;
         }
-        row[(sg * C::QA) / 4 + i4] = make_float4(v[0], v[1], v[2], v[3]);
+        if (NLEM_DBG_OK(j * C::DP + sg * C::QA + 4 * i4 + 3, C::SZ_PTS, kDbgPointRow))
+          row[(sg * C::QA) / 4 + i4] = make_float4(v[0], v[1], v[2], v[3]);
       }
     }
   }
@@ -189,7 +197,8 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
     if (slot < slice_real<C>(sg, C::D)) {
       const int q = sg * C::Q + slot;
       const int qr = q / K, qc = q - qr * K;
-      v = sm.tile[(ir - r0 + qr) * TC + (ic - c0 + qc)];
+      const int ti = (ir - r0 + qr) * TC + (ic - c0 + qc);
+      v = NLEM_DBG_OK(ti, TR * TC, kDbgTileRead) ? sm.tile[ti] : 0.f;
     }
     sm.pcv[i] = v;
   }

@@ -14,6 +14,7 @@
 #include "../../include/nlem.h"
 #include "ctx.h"
 #include "kernels.h"
+#include "trace.h"
 #include "warmstart.h"
 
 struct nlem_warmstart {
@@ -268,6 +269,7 @@ int nlem_ws_load(nlem_warmstart* ws, const char* path) {
 }
 
 int nlem_ws_forward(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, float* y, void* stream) {
+  NLEM_TRACE("nlem_ws_forward");
   if (!ctx || !ws || !feats || !y || B < 0) return wfail(NLEM_ERR_INVALID, "bad arguments");
   cudaSetDevice(ctx->device);
   const int rc = nlemk::ws_forward(ws->m, feats, B, y, nullptr, nullptr, nullptr, ctx->sm_count, (cudaStream_t)stream);
@@ -276,6 +278,7 @@ int nlem_ws_forward(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long 
 
 int nlem_ws_loss_grad(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long B,
                       float* loss, float* grad, void* stream) {
+  NLEM_TRACE("nlem_ws_loss_grad");
   if (!ctx || !ws || !feats || !targets || B < 1) return wfail(NLEM_ERR_INVALID, "bad arguments");
   cudaSetDevice(ctx->device);
   nlemk::WsScratch& sc = ws->sc;
@@ -310,6 +313,7 @@ int nlem_ws_loss_grad(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, con
 
 int nlem_ws_train_step(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long B,
                        float lr, float* loss, void* stream) {
+  NLEM_TRACE("nlem_ws_train_step");
   int rc = nlem_ws_loss_grad(ctx, ws, feats, targets, B, loss, nullptr, stream);
   if (rc) return rc;
   rc = nlemk::ws_adam(ws->m, ws->sc.grad, lr, ctx->sm_count, (cudaStream_t)stream);
@@ -326,6 +330,7 @@ static unsigned long long ws_mix64(unsigned long long z) {
 
 int nlem_ws_train(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const float* targets, long long N,
                   int epochs, int batch, float lr, unsigned long long seed, float* epoch_loss, void* stream) {
+  NLEM_TRACE("nlem_ws_train");
   if (!ctx || !ws || !feats || !targets || N < 1 || epochs < 0 || batch < 1 || !(lr > 0.f) || !std::isfinite(lr))
     return wfail(NLEM_ERR_INVALID, "bad arguments");
   if (N > 2147483647LL) return wfail(NLEM_ERR_UNSUPPORTED, "at most 2^31 - 1 samples");
@@ -376,6 +381,7 @@ int nlem_ws_train(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, const f
 
 int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long long B, nlem_box box, float* y,
                     float* x0, float* rho, void* stream) {
+  NLEM_TRACE("nlem_ws_predict");
   if (!ctx || !ws || !feats || !y || !x0 || !rho || B < 0) return wfail(NLEM_ERR_INVALID, "bad arguments");
   cudaSetDevice(ctx->device);
   int rc = nlemk::ws_forward(ws->m, feats, B, y, nullptr, nullptr, nullptr, ctx->sm_count, (cudaStream_t)stream);
@@ -385,6 +391,7 @@ int nlem_ws_predict(nlem_ctx* ctx, nlem_warmstart* ws, const float* feats, long 
 
 int nlem_features(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int patch, int window, float h,
                   const int* pixels, long long npix, float* feats, void* stream) {
+  NLEM_TRACE("nlem_features");
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (!feats) return wfail(NLEM_ERR_INVALID, "feats is NULL");
@@ -411,6 +418,7 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
                     float rho, int iters, nlem_box box, const nlem_options* opt, const int* pixels, long long npix,
                     const float* x0, const float* rho_pix, float* out, int* iters_used, float* residual,
                     float* z_out, void* stream) {
+  NLEM_TRACE("nlem_denoise_ex");
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (!out) return wfail(NLEM_ERR_INVALID, "out is NULL");
@@ -448,6 +456,7 @@ int nlem_ws_labels(nlem_ctx* ctx, const float* image, int H, int W, int pitch, i
                    nlem_box box, const int* pixels, long long n, const float* rho_grid, int n_rho, float tol,
                    int check_every, int cap, float tight_tol, int tight_cap, const float* feats, float* targets,
                    long long* rho_counts, void* stream) {
+  NLEM_TRACE("nlem_ws_labels");
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (n < 0) return wfail(NLEM_ERR_INVALID, "n must be >= 0");
@@ -520,6 +529,7 @@ int nlem_ws_labels(nlem_ctx* ctx, const float* image, int H, int W, int pitch, i
 int nlem_denoise_warm(nlem_ctx* ctx, nlem_warmstart* ws, const float* image, int H, int W, int pitch, int patch,
                       int window, float h, float rho_fallback, int iters, nlem_box box, const nlem_options* opt,
                       float* out, int* iters_used, long long* fallback_count, void* stream) {
+  NLEM_TRACE("nlem_denoise_warm");
   int rc = check_nlem_args(ctx, image, H, W, pitch, patch, window, h);
   if (rc) return rc;
   if (!ws || !out || !iters_used) return wfail(NLEM_ERR_INVALID, "ws, out and iters_used must be non-NULL");
