@@ -16,7 +16,10 @@
 // Layout: G consecutive lanes share a point; lane g of a group owns coordinate slice
 // [g*Q, g*Q+Q) (the last slice may be shorter: phantom slots read as 0).  A lane owns P
 // points j = pg + p*NG (pg = its group, NG = groups per CTA), so h[P][Q] lives in registers.
-// Points a_j sit in shared memory as [j][slice][QA] float rows (16-byte aligned slices).
+// Points sit in shared memory as [j][slice][QA] float rows (16-byte aligned slices) holding -a_j
+// (NEG = true: the update h = s e - a then takes the loaded value as the FMA addend as it is) or
+// a_j (NEG = false).  Both give the same arithmetic, bit for bit; the register allocation, and
+// with it the speed, differs per kernel, so each kernel takes the sign it measured faster with.
 // The d-vector sum over all points uses a two-level shared-memory column reduction; one warp
 // then forms z+, c+ and, on check iterations, the relative residuals.
 #pragma once
@@ -288,7 +291,7 @@ __device__ __forceinline__ void project_zv(const Smem<C>& sm, int d, const PJ& p
 // Weighted sum of the points (sum_j w_j a_j) and sum_j w_j, with w_j = weight of point slot
 // j taken from wreg[p] (0 for inactive slots).  Writes z0 = P_C(sum w a / sum w) into zv and
 // cv (c(0) = z(0)), zeroes sgv.  If sum w == 0 the plain mean of the n points is used.
-template <class C, class X = NoExchange, class PJ = ScalarBox>
+template <class C, class X = NoExchange, class PJ = ScalarBox, bool NEG = false>
 __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P], int n, int d,
                                     const SolveParams& prm, const PJ& pj = PJ()) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31;
@@ -304,7 +307,7 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
       load_slice<C>(sm.pts + j * C::DP + g * C::QA, last, a);
       const float w = pass == 0 ? wreg[p] : (j < n ? 1.f : 0.f);
 #pragma unroll
-      for (int q = 0; q < C::Q; ++q) acc[q] = fmaf(w, a[q], acc[q]);
+      for (int q = 0; q < C::Q; ++q) acc[q] = fmaf(NEG ? -w : w, a[q], acc[q]);
       if (g == 0) acc[C::Q] += w;
     }
     float4 t0, t1;
@@ -385,7 +388,7 @@ __device__ void weighted_mean_start(const Smem<C>& sm, const float (&wreg)[C::P]
 //   the residuals of the stopping rule in the w-weighted norm (n -> W, each point's terms
 //   times w_k), so the reformulation above holds with every sum over k weighted by w_k.
 // If every weight is zero the weights are taken as 1.
-template <class C, bool SPLIT = false, class X = NoExchange, class PJ = ScalarBox, bool WPEN = false>
+template <class C, bool SPLIT = false, class X = NoExchange, class PJ = ScalarBox, bool WPEN = false, bool NEG = false>
 __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm, const PJ& pj = PJ()) {
   static_assert(!SPLIT || C::G == 2, "the split rsqrt pairs the two lanes of a point");
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
@@ -422,8 +425,8 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     float a[C::Q];
     load_slice<C>(sm.pts + j * C::DP + g * C::QA, last, a);
 #pragma unroll
-    for (int k = 0; k < NP2; ++k) h2[p][k] = make_float2(-a[2 * k], -a[2 * k + 1]);
-    h1[p] = (C::Q % 2) ? -a[C::Q - 1] : 0.f;
+    for (int k = 0; k < NP2; ++k) h2[p][k] = NEG ? make_float2(a[2 * k], a[2 * k + 1]) : make_float2(-a[2 * k], -a[2 * k + 1]);
+    h1[p] = (C::Q % 2) ? (NEG ? a[C::Q - 1] : -a[C::Q - 1]) : 0.f;
   }
 
   int it = 0;
@@ -530,7 +533,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
       for (int p = 0; p < C::P; ++p) {
         const float* arow = sm.pts + (pg + p * C::NG) * C::DP + g * C::QA;
         const float oms = 1.f - s[p];
-        const float2 oms2 = make_float2(oms, oms);
+        const float2 oms2 = make_float2(oms, oms), noms2 = make_float2(-oms, -oms);
         float2 dd2 = make_float2(0.f, 0.f);
         float dd1 = 0.f;
 #pragma unroll
@@ -542,11 +545,13 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
             const int q0 = 4 * i + 2 * jh;
             const float2 a2 = jh == 0 ? make_float2(a4.x, a4.y) : make_float2(a4.z, a4.w);
             const float2 c2 = jh == 0 ? make_float2(c4.x, c4.y) : make_float2(c4.z, c4.w);
+            // with rows of -a, (-(1-s)) e + (c - a) is the negated difference, with the same square
             if (q0 + 1 < C::Q) {
-              const float2 dq2 = __ffma2_rn(oms2, h2[p][q0 / 2], __fadd2_rn(a2, make_float2(-c2.x, -c2.y)));
+              const float2 dq2 = NEG ? __ffma2_rn(noms2, h2[p][q0 / 2], __fadd2_rn(a2, c2))
+                                     : __ffma2_rn(oms2, h2[p][q0 / 2], __fadd2_rn(a2, make_float2(-c2.x, -c2.y)));
               dd2 = __ffma2_rn(dq2, dq2, dd2);
             } else if (q0 < C::Q) {
-              const float dq = fmaf(oms, h1[p], a2.x - c2.x);
+              const float dq = NEG ? fmaf(-oms, h1[p], a2.x + c2.x) : fmaf(oms, h1[p], a2.x - c2.x);
               if constexpr (WPEN)
                 dd1 = fmaf(dq, dq, dd1);
               else
@@ -589,7 +594,8 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
               const int q0 = 4 * i + 2 * jh;
-              const float2 na2 = jh == 0 ? make_float2(-a4.x, -a4.y) : make_float2(-a4.z, -a4.w);
+              const float2 a2 = jh == 0 ? make_float2(a4.x, a4.y) : make_float2(a4.z, a4.w);
+              const float2 na2 = NEG ? a2 : make_float2(-a2.x, -a2.y);
               if (q0 + 1 < C::Q) {
                 accp[jh] = __ffma2_rn(wp2, h2[p][q0 / 2], accp[jh]);
                 h2[p][q0 / 2] = __ffma2_rn(sp2, h2[p][q0 / 2], na2);
@@ -810,7 +816,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 // accumulated in double on the GPU.  Uses the wred region as scratch (CAP doubles for the
 // distances).  wfun(j) returns the weight of point j in double: the caller's input weight for
 // standalone problems, exp(-||P_i - P_j||^2 / h^2) recomputed in double for NLEM.
-template <class C, class WF>
+template <class C, class WF, bool NEG = false>
 __device__ void fp64_check(const Smem<C>& sm, int n, int d, const SolveParams& prm, const WF& wfun,
                            double& F, double& R) {
   const int t = threadIdx.x;
@@ -824,7 +830,8 @@ __device__ void fp64_check(const Smem<C>& sm, int n, int d, const SolveParams& p
     double r2 = 0.0;
     for (int q = 0; q < d; ++q) {
       const int sg = q / C::Q, i = q - sg * C::Q;
-      const double e = (double)sm.zv[sg * C::QA + i] - (double)sm.pts[j * C::DP + sg * C::QA + i];
+      const double a = (double)sm.pts[j * C::DP + sg * C::QA + i];
+      const double e = (double)sm.zv[sg * C::QA + i] + (NEG ? a : -a);   // z - a
       r2 += e * e;
     }
     const double r = sqrt(r2);
@@ -844,7 +851,10 @@ __device__ void fp64_check(const Smem<C>& sm, int n, int d, const SolveParams& p
     const int sg = q / C::Q, i = q - sg * C::Q;
     const double z = (double)sm.zv[sg * C::QA + i];
     double gq = 0.0;
-    for (int j = 0; j < n; ++j) gq += coef[j] * (z - (double)sm.pts[j * C::DP + sg * C::QA + i]);
+    for (int j = 0; j < n; ++j) {
+      const double a = (double)sm.pts[j * C::DP + sg * C::QA + i];
+      gq += coef[j] * (z + (NEG ? a : -a));
+    }
     gvec[q] = gq;
     g2 += gq * gq;
   }

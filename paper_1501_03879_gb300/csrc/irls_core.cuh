@@ -25,7 +25,7 @@ namespace nlemk {
 // inactive slots) and zv = cv = x(0) (phantom slots zero).  Runs exactly prm.iters steps.  On
 // return zv holds x and cv the last step; scal[2] = steps run; scal[3] = ||x(T) - x(T-1)|| /
 // ||x(T)|| of the last step (0 when no step ran).
-template <class C>
+template <class C, bool NEG = false>
 __device__ void irls_iterate(const Smem<C>& sm, int n, int d, const SolveParams& prm) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>(), lane = t & 31, warp = t >> 5;
   const bool last = (g == C::G - 1);
@@ -41,8 +41,9 @@ __device__ void irls_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     float a[C::Q];
     load_slice<C>(sm.pts + j * C::DP + g * C::QA, last, a);
 #pragma unroll
-    for (int k = 0; k < NP2; ++k) e2[p][k] = make_float2(-a[2 * k], -a[2 * k + 1]);
-    e1[p] = (C::Q % 2) ? -a[C::Q - 1] : 0.f;
+    // e = -a: the rows hold -a (NEG) or a
+    for (int k = 0; k < NP2; ++k) e2[p][k] = NEG ? make_float2(a[2 * k], a[2 * k + 1]) : make_float2(-a[2 * k], -a[2 * k + 1]);
+    e1[p] = (C::Q % 2) ? (NEG ? a[C::Q - 1] : -a[C::Q - 1]) : 0.f;
     lam[p] = sm.lam[j];
   }
 

@@ -180,12 +180,12 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
     for (int q = 0; q < NQ; ++q) {
       const float4 a4 = reinterpret_cast<const float4*>(arow)[q];
       const float4 b4 = reinterpret_cast<const float4*>(brow)[q];
-      hA[p][2 * q] = f2(-a4.x, -a4.y);
-      hA[p][2 * q + 1] = f2(-a4.z, -a4.w);
-      hB[p][2 * q] = f2(-b4.x, -b4.y);
-      hB[p][2 * q + 1] = f2(-b4.z, -b4.w);
+      hA[p][2 * q] = f2(a4.x, a4.y);
+      hA[p][2 * q + 1] = f2(a4.z, a4.w);
+      hB[p][2 * q] = f2(b4.x, b4.y);
+      hB[p][2 * q + 1] = f2(b4.z, b4.w);
     }
-    hT[p] = tl ? f2(-arow[QM], -brow[QM]) : f2(0.f, 0.f);
+    hT[p] = tl ? f2(arow[QM], brow[QM]) : f2(0.f, 0.f);
   }
 
   for (int it = 1; it <= prm.iters; ++it) {
@@ -300,16 +300,16 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
           const float4 a4 = reinterpret_cast<const float4*>(arow)[q];
           const float4 b4 = reinterpret_cast<const float4*>(brow)[q];
           const float4 cA = cv4[q], cB = cv4[4 + q];
-          float2 x = __ffma2_rn(oA2, hA[p][2 * q], f2(a4.x - cA.x, a4.y - cA.y));
+          float2 x = __ffma2_rn(oA2, hA[p][2 * q], f2(-a4.x - cA.x, -a4.y - cA.y));
           dA2 = __ffma2_rn(x, x, dA2);
-          x = __ffma2_rn(oA2, hA[p][2 * q + 1], f2(a4.z - cA.z, a4.w - cA.w));
+          x = __ffma2_rn(oA2, hA[p][2 * q + 1], f2(-a4.z - cA.z, -a4.w - cA.w));
           dA2 = __ffma2_rn(x, x, dA2);
-          x = __ffma2_rn(oB2, hB[p][2 * q], f2(b4.x - cB.x, b4.y - cB.y));
+          x = __ffma2_rn(oB2, hB[p][2 * q], f2(-b4.x - cB.x, -b4.y - cB.y));
           dB2 = __ffma2_rn(x, x, dB2);
-          x = __ffma2_rn(oB2, hB[p][2 * q + 1], f2(b4.z - cB.z, b4.w - cB.w));
+          x = __ffma2_rn(oB2, hB[p][2 * q + 1], f2(-b4.z - cB.z, -b4.w - cB.w));
           dB2 = __ffma2_rn(x, x, dB2);
         }
-        const float2 tv = tl ? f2(arow[QM], brow[QM]) : f2(0.f, 0.f);
+        const float2 tv = tl ? f2(-arow[QM], -brow[QM]) : f2(0.f, 0.f);
         const float2 x = __ffma2_rn(f2(oA, oB), hT[p], f2(tv.x - cT.x, tv.y - cT.y));
         ddA += dA2.x + dA2.y + x.x * x.x;
         ddB += dB2.x + dB2.y + x.y * x.y;
@@ -346,18 +346,18 @@ __device__ void pair_iterate(const Sm& sm, int nA, int nB, int nex, const SolveP
           if (q == NQ) {
             const float2 sT = f2(sA[p], sB[p]);
             aT = __ffma2_rn(sT, hT[p], aT);
-            hT[p] = __ffma2_rn(sT, hT[p], f2(-a4.x, -b4.x));
+            hT[p] = __ffma2_rn(sT, hT[p], f2(a4.x, b4.x));
             continue;
           }
           const float2 sA2 = f2(sA[p], sA[p]), sB2 = f2(sB[p], sB[p]);
           aA0 = __ffma2_rn(sA2, hA[p][2 * q], aA0);
-          hA[p][2 * q] = __ffma2_rn(sA2, hA[p][2 * q], f2(-a4.x, -a4.y));
+          hA[p][2 * q] = __ffma2_rn(sA2, hA[p][2 * q], f2(a4.x, a4.y));
           aA1 = __ffma2_rn(sA2, hA[p][2 * q + 1], aA1);
-          hA[p][2 * q + 1] = __ffma2_rn(sA2, hA[p][2 * q + 1], f2(-a4.z, -a4.w));
+          hA[p][2 * q + 1] = __ffma2_rn(sA2, hA[p][2 * q + 1], f2(a4.z, a4.w));
           aB0 = __ffma2_rn(sB2, hB[p][2 * q], aB0);
-          hB[p][2 * q] = __ffma2_rn(sB2, hB[p][2 * q], f2(-b4.x, -b4.y));
+          hB[p][2 * q] = __ffma2_rn(sB2, hB[p][2 * q], f2(b4.x, b4.y));
           aB1 = __ffma2_rn(sB2, hB[p][2 * q + 1], aB1);
-          hB[p][2 * q + 1] = __ffma2_rn(sB2, hB[p][2 * q + 1], f2(-b4.z, -b4.w));
+          hB[p][2 * q + 1] = __ffma2_rn(sB2, hB[p][2 * q + 1], f2(b4.z, b4.w));
         }
         if (q < NQ)
           u[q] = rs_step(make_float4(aA0.x, aA0.y, aA1.x, aA1.y), make_float4(aB0.x, aB0.y, aB1.x, aB1.y), 4);
@@ -483,7 +483,7 @@ __device__ void pair_fp64(const Sm& sm, int X, int nex, const SolveParams& prm, 
     const float* row = row_of(j);
     double r2 = 0.0, dw = 0.0;
     for (int q = 0; q < D; ++q) {
-      const double a = (double)row[q];
+      const double a = -(double)row[q];
       const double e = (double)sm.zv[vidx(q, X)] - a;
       const double u = (double)sm.pcv[vidx(q, X)] - a;
       r2 += e * e;
@@ -505,7 +505,7 @@ __device__ void pair_fp64(const Sm& sm, int X, int nex, const SolveParams& prm, 
     const double z = (double)sm.zv[vidx(q, X)];
     double gq = 0.0;
     for (int j = 0; j < CAP; ++j)
-      if (coef[j] != 0.0) gq += coef[j] * (z - (double)row_of(j)[q]);
+      if (coef[j] != 0.0) gq += coef[j] * (z + (double)row_of(j)[q]);
     gvec[q] = gq;
     g2 += gq * gq;
   }
@@ -623,7 +623,7 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
       for (int c = 0; c < 4; ++c) {
         const int q = 4 * i4 + c;
         const int ti = r * TC + (u - a0) + (q / K) * TC + (q % K);
-        v[c] = (u >= 0 && q < D && NLEM_DBG_OK(ti, TR * TC, kDbgPairTile)) ? tp[(q / K) * TC + (q % K)] : 0.f;
+        v[c] = (u >= 0 && q < D && NLEM_DBG_OK(ti, TR * TC, kDbgPairTile)) ? -tp[(q / K) * TC + (q % K)] : 0.f;
       }
       if (NLEM_DBG_OK(dst - sm.pts + 4 * i4 + 3, OFF_LAM - OFF_PTS, kDbgPairRow))
         row4[i4] = make_float4(v[0], v[1], v[2], v[3]);
@@ -657,13 +657,13 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
         const float4 pa = pc4[q], pb = pc4[4 + q];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const float ea = f4get(pa, c) - f4get(a4, c), eb = f4get(pb, c) - f4get(b4, c);
+          const float ea = f4get(pa, c) + f4get(a4, c), eb = f4get(pb, c) + f4get(b4, c);
           dA = fmaf(ea, ea, dA);
           dB = fmaf(eb, eb, dB);
         }
       }
       if (tl) {
-        const float ea = pT.x - arow[QM], eb = pT.y - brow[QM];
+        const float ea = pT.x + arow[QM], eb = pT.y + brow[QM];
         dA = fmaf(ea, ea, dA);
         dB = fmaf(eb, eb, dB);
       }
@@ -705,14 +705,14 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
         for (int q = 0; q < NQ; ++q) {
           const float4 a4 = reinterpret_cast<const float4*>(arow)[q];
           const float4 b4 = reinterpret_cast<const float4*>(brow)[q];
-          accA[q] = make_float4(fmaf(wA[p], a4.x, accA[q].x), fmaf(wA[p], a4.y, accA[q].y),
-                                fmaf(wA[p], a4.z, accA[q].z), fmaf(wA[p], a4.w, accA[q].w));
-          accB[q] = make_float4(fmaf(wB[p], b4.x, accB[q].x), fmaf(wB[p], b4.y, accB[q].y),
-                                fmaf(wB[p], b4.z, accB[q].z), fmaf(wB[p], b4.w, accB[q].w));
+          accA[q] = make_float4(fmaf(-wA[p], a4.x, accA[q].x), fmaf(-wA[p], a4.y, accA[q].y),
+                                fmaf(-wA[p], a4.z, accA[q].z), fmaf(-wA[p], a4.w, accA[q].w));
+          accB[q] = make_float4(fmaf(-wB[p], b4.x, accB[q].x), fmaf(-wB[p], b4.y, accB[q].y),
+                                fmaf(-wB[p], b4.z, accB[q].z), fmaf(-wB[p], b4.w, accB[q].w));
         }
         if (tl) {
-          accT.x = fmaf(wA[p], arow[QM], accT.x);
-          accT.y = fmaf(wB[p], brow[QM], accT.y);
+          accT.x = fmaf(-wA[p], arow[QM], accT.x);
+          accT.y = fmaf(-wB[p], brow[QM], accT.y);
         }
         swA += wA[p];
         swB += wB[p];
