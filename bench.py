@@ -111,12 +111,10 @@ KERNEL_SOURCES = {
                         _CSRC + "shapes.h"],
 }
 PROFILED = {
-    "nlem_pair_kernel": {"sources": "ddd3083535f597a7", "traffic": (132608 + 0) * 16, "fma_pipe_pct": 47.81,
-                         "issue_pct": 46.53, "smem_wavefront_pct": 42.13},
-    "nlem_kernel": {"sources": "54e40d8b984cc1f2", "traffic": (132864 + 236544) * 16, "fma_pipe_pct": 43.58,
-                    "issue_pct": 37.33, "smem_wavefront_pct": 67.65},
-    "em_batch_kernel": {"sources": "bd61b46b57b4306d", "traffic": (361708800 + 4032768) * 64, "fma_pipe_pct": 41.57,
-                        "issue_pct": 35.43, "smem_wavefront_pct": 66.74},
+    "nlem_pair_kernel": {"sources": "a3cfbe862ae740e4", "traffic": (133376 + 0) * 16, "fma_pipe_pct": 48.09,
+                         "issue_pct": 45.77, "smem_wavefront_pct": 41.37},
+    "em_batch_kernel": {"sources": "ce399dc74d7e2592", "traffic": (362494976 + 3801856) * 64, "fma_pipe_pct": 40.76,
+                        "issue_pct": 34.87, "smem_wavefront_pct": 65.80},
 }
 
 
