@@ -553,11 +553,13 @@ __device__ __forceinline__ int reflect(int x, int N) { return x < 0 ? -x : (x >=
 
 // One pixel pair: tile of the reflect-padded image around the union of the two clipped search
 // windows -> point rows -> weights of both problems -> start points -> Algorithm 1 -> the
-// centre coordinates.  Ends with a barrier.
+// centre coordinates.  EX: the caller's per-pixel start points, penalties and solution patches
+// (ex) are taken; the plain instance compiles without them.  Ends with a barrier.
+template <bool EX>
 __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long item,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
-                           double* __restrict__ obj64, double* __restrict__ kkt64) {
+                           double* __restrict__ obj64, double* __restrict__ kkt64, const PixelExtra& ex) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane_g(), pg = lane_pg();
   const bool tl = (g == G - 1);
   const int WP = (W + 1) / 2, R = (S - 1) / 2;
@@ -639,6 +641,10 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
     sm.pcv[vcol(col) * 4 + slot] = v;
   }
   __syncthreads();
+  // each pixel's penalty: the caller's per-pixel one, else the launch's
+  const long long pix0 = (long long)y * W + x;
+  const float imuA = (EX && ex.rho) ? 1.f / __ldg(ex.rho + pix0) : prm.inv_mu;
+  const float imuB = (EX && ex.rho && hasB) ? 1.f / __ldg(ex.rho + pix0 + 1) : prm.inv_mu;
   // weights w_j = exp(-||P_X - P_j||^2 / h^2) of both problems (zero where X has no point j)
   float wA[P], wB[P];
   {
@@ -672,13 +678,27 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
       const int fl = sm.flag[j];
       wA[p] = (fl & 1) ? expf(-dA * inv_h2) : 0.f;
       wB[p] = (fl & 2) ? expf(-dB * inv_h2) : 0.f;
-      if (g == 0) sm.lam[lam_at(j)] = f2(wA[p] * prm.inv_mu, wB[p] * prm.inv_mu);
+      if (g == 0) sm.lam[lam_at(j)] = f2(wA[p] * imuA, wB[p] * imuB);
     }
   }
   float4* zv4 = reinterpret_cast<float4*>(sm.zv);
   float4* cvw = reinterpret_cast<float4*>(sm.cv);
   float4* sgv4 = reinterpret_cast<float4*>(sm.sgv);
-  if (init_mode == 1) {   // the noisy patches, projected onto C
+  if (EX && ex.x0) {   // the caller's start points of both pixels, projected onto C
+    if (t < NCOL) {
+      const int sg = t >> 3, c = t & 7, X = c >> 2, cc = c & 3;
+      const long long pixX = (long long)y * W + x + X;
+      float zz[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int q = cc < 3 ? sg * QM + 4 * cc + i : ((sg == G - 1 && i == 0) ? 4 * G * NQ : -1);
+        zz[i] = (q >= 0 && (X == 0 || hasB)) ? clampf(__ldg(ex.x0 + pixX * D + q), prm.lo, prm.hi) : 0.f;
+      }
+      zv4[vcol(t)] = cvw[vcol(t)] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+      sgv4[vcol(t)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+  } else if (init_mode == 1) {   // the noisy patches, projected onto C
     if (t < NCOL) {
       const float4 pc = reinterpret_cast<const float4*>(sm.pcv)[vcol(t)];
       const int cc = t & 3, nreal = cc < 3 ? 4 : ((t >> 3) == G - 1 ? 1 : 0);
@@ -744,6 +764,12 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
   }
   pair_iterate(sm, nA, nB, nex, prm);
   const long long pixA = (long long)y * W + x;
+  if (EX && ex.z_out) {   // the whole solution patch of each pixel
+    for (int i = t; i < 2 * D; i += NT) {
+      const int X = i / D, q = i - X * D;
+      if (X == 0 || hasB) ex.z_out[(pixA + X) * D + q] = sm.zv[vidx(q, X)];
+    }
+  }
   if (t == 0) {
     out[pixA] = sm.zv[vidx(D / 2, 0)];
     if (iters_used) iters_used[pixA] = (int)sm.scal[2];
@@ -767,27 +793,28 @@ __device__ void pair_pixel(const Sm& sm, const float* __restrict__ img, int H, i
   __syncthreads();
 }
 
+template <bool EX>
 __global__ void __launch_bounds__(NT, 1)
 nlem_pair_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
                  SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
-                 float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64) {
+                 float* __restrict__ resid, double* __restrict__ obj64, double* __restrict__ kkt64, PixelExtra ex) {
   extern __shared__ float4 smem_raw[];
   const Sm sm(reinterpret_cast<float*>(smem_raw));
   const long long items = (long long)H * ((W + 1) / 2);
   for (long long it = blockIdx.x; it < items; it += gridDim.x)
-    pair_pixel(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, it, out, iters_used, resid, obj64, kkt64);
+    pair_pixel<EX>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, it, out, iters_used, resid, obj64, kkt64, ex);
 }
 
 }  // namespace pairk
 
 bool nlem_pair_eligible(const NlemLaunch& L) {
-  return L.patch == pairk::K && L.S >= 1 && L.S <= 2 * ((pairk::RMAX - 1) / 2) + 1 && !L.wtab && !L.pix_list &&
-         !L.ex.x0 && !L.ex.rho && !L.ex.z_out;
+  return L.patch == pairk::K && L.S >= 1 && L.S <= 2 * ((pairk::RMAX - 1) / 2) + 1 && !L.wtab && !L.pix_list;
 }
 
 int launch_nlem_pair_k7(const NlemLaunch& L) {
   if (!nlem_pair_eligible(L)) return -1;
-  auto kern = pairk::nlem_pair_kernel;
+  const bool ex = L.ex.x0 || L.ex.rho || L.ex.z_out;
+  auto kern = ex ? pairk::nlem_pair_kernel<true> : pairk::nlem_pair_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pairk::SMEM_BYTES);
   if (e != cudaSuccess) return (int)e;
   const long long items = (long long)L.H * ((L.W + 1) / 2);
@@ -796,7 +823,7 @@ int launch_nlem_pair_k7(const NlemLaunch& L) {
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, pairk::NT, pairk::SMEM_BYTES, L.stream>>>(L.img, L.H, L.W, L.pitch, L.S, L.inv_h2,
                                                                    L.inv_h2_exact, L.prm, L.init_mode, L.out,
-                                                                   L.iters_used, L.resid, L.obj64, L.kkt64);
+                                                                   L.iters_used, L.resid, L.obj64, L.kkt64, L.ex);
   return (int)cudaGetLastError();
 }
 

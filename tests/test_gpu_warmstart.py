@@ -169,6 +169,29 @@ def test_per_pixel_start_and_penalty(nl):
         assert rel_err(out[lin], zo[24]) <= TOL
 
 
+def test_per_pixel_start_and_penalty_on_pixel_pairs(nl):
+    """Every pixel of an image with per-pixel x0 and rho and a 21x21 window (7x7 patches: the pixel-pair
+    kernel, which also writes the whole solution patches) equals the oracle started from the same point
+    with the same penalty; odd width, so the last pair has no second pixel."""
+    g, _ = synth.noisy_image(8110, 26, 31, 25.0)
+    H, W = g.shape
+    h = 250.0
+    img = torch.from_numpy(g).to(DEV)
+    rng = np.random.default_rng(7)
+    x0 = rng.uniform(-10, 265, (H * W, 49)).astype(np.float32)
+    rho = np.exp(rng.uniform(np.log(1e-3), 0, H * W)).astype(np.float32)
+    r = nl.nlem_denoise_ex(img, 7, 21, h, iters=40, x0=torch.from_numpy(x0).to(DEV),
+                           rho_pix=torch.from_numpy(rho).to(DEV), z_out=True)
+    out = r["out"].cpu().numpy().reshape(-1)
+    z = r["z"].cpu().numpy()
+    worst = 0.0
+    for lin in range(H * W):
+        pts, w, _ = oracle.nlem_problem(g, 7, 21, h, lin)
+        zo, *_ = oracle.em_admm(pts, w, 0.0, 255.0, float(rho[lin]), 40, z0=np.clip(x0[lin], 0, 255))
+        worst = max(worst, rel_err(z[lin], zo).max(), rel_err(out[lin], zo[24]))
+    assert worst <= TOL, worst
+
+
 def test_pixel_list_entries_outside_the_image_are_skipped(nl):
     """A pixel list with entries outside [0, H*W) (negative, past the end) and a duplicate: the valid
     pixels get the same values as the whole-image solve, the other outputs keep what they held."""
