@@ -111,8 +111,8 @@ KERNEL_SOURCES = {
                         _CSRC + "shapes.h"],
 }
 PROFILED = {
-    "nlem_pair_kernel": {"sources": "a3cfbe862ae740e4", "traffic": (133376 + 0) * 16, "fma_pipe_pct": 48.09,
-                         "issue_pct": 45.77, "smem_wavefront_pct": 41.37},
+    "nlem_pair_kernel": {"sources": "ca4c4cf06576c924", "traffic": (132864 + 0) * 16, "fma_pipe_pct": 48.10,
+                         "issue_pct": 45.77, "smem_wavefront_pct": 41.38},
     "em_batch_kernel": {"sources": "ce399dc74d7e2592", "traffic": (362494976 + 3801856) * 64, "fma_pipe_pct": 40.76,
                         "issue_pct": 34.87, "smem_wavefront_pct": 65.80},
 }
