@@ -40,6 +40,8 @@ extern "C" {
 #define NLEM_SOLVER_ADMM 0          /* EM-ADMM, Algorithm 1 (Sec. 2) */
 #define NLEM_SOLVER_IRLS 1          /* IRLS on the smooth surrogate of Eq. 2 (Sec. 1), the comparison
                                        method of Sec. 3 (nlem_denoise only) */
+#define NLEM_SOLVER_FAST 2          /* accelerated EM-ADMM: Algorithm 1's steps with momentum and
+                                       restart (see nlem_options.restart_every) */
 
 #define NLEM_PENALTY_UNIFORM 0       /* one penalty mu = rho for every constraint x_k = z: Algorithm 1 */
 #define NLEM_PENALTY_WEIGHTED 1      /* a penalty per constraint, mu_k = rho * w_k (see nlem_options) */
@@ -80,6 +82,24 @@ typedef struct {
                          (and em_solve, em_solve_batch_host) with d = 49 and for nlem_denoise,
                          nlem_denoise_host and nlem_denoise_ex with 7x7 patches on the one-pixel
                          layout; -5 elsewhere (-1 with IRLS) */
+  int restart_every;  /* NLEM_SOLVER_FAST only, >= 0.  The accelerated solver (Sec. 4 names accelerated
+                         ADMM as future work) is fast ADMM with restart (Goldstein, O'Donoghue, Setzer
+                         and Baraniuk 2014): each step is one step of Algorithm 1 from an extrapolated
+                         point (z^, y^), followed by c = rho * n * ||z - z^||^2, the z-part of their
+                         combined residual (its y-part lies below what FP32 iterates resolve near
+                         convergence).  restart_every = 0 (default):
+                         if c < 0.999 * c_prev, alpha+ = (1 + sqrt(1 + 4 alpha^2)) / 2 and z^, y^ step
+                         past the new iterate by (alpha - 1) / alpha+ times its change; otherwise
+                         alpha = 1, z^ and y^ restart from the previous iterate and c_prev is divided
+                         by 0.999.  restart_every = k >= 1: the fixed restart of O'Donoghue and Candes
+                         (2015), restarting after every k-th step and taking the momentum otherwise.
+                         Stopping rule and residuals as Algorithm 1's at each step's x, y, z, with the
+                         step's own z-change z - z^ in place of z - z_prev (the same without
+                         extrapolation).  Compiled for em_solve_batch (and em_solve_batch_host)
+                         with d = 49 and n <= 448, and for nlem_denoise, nlem_denoise_host and
+                         nlem_denoise_ex with 7x7 patches and windows of at most 448 points on the
+                         one-pixel layout (AUTO takes it; PAIR is -5); -5 elsewhere and with
+                         per-point penalties */
 } nlem_options;
 
 void nlem_options_default(nlem_options* opt);

@@ -80,7 +80,7 @@ def _load():
     lib.orc_project_box.argtypes = [D, c_int, c_double, c_double, D]
     lib.orc_project_set.argtypes = [D, c_int, c_int, D, D, c_double, D]
     lib.orc_em_admm_fast.argtypes = [D, D, c_int, c_int, c_double, c_double, c_double, c_int, D, c_double, c_int,
-                                     c_double, D, ctypes.POINTER(c_int), D, D, ctypes.POINTER(c_int)]
+                                     c_double, c_int, c_int, D, ctypes.POINTER(c_int), D, D, ctypes.POINTER(c_int), D]
     lib.orc_em_admm_fast.restype = c_int
     lib.orc_em_admm_set.argtypes = [D, D, c_int, c_int, c_int, D, D, c_double, c_double, c_int, D, c_double, c_int,
                                     D, ctypes.POINTER(c_int), D, D]
@@ -96,10 +96,11 @@ def _load():
     lib.orc_weiszfeld.argtypes = [D, D, c_int, c_int, D, c_int, D, D]
     lib.orc_irls.argtypes = [D, D, c_int, c_int, c_double, c_double, D, c_double, c_int, D, D]
     lib.orc_em_admm_batch.argtypes = [F, F, c_ll, c_int, c_int, c_double, c_double, c_double, c_int,
-                                      F, c_double, c_int, D, I, D, D, c_int, c_int]
+                                      F, c_double, c_int, D, I, D, D, c_int, c_int, I, D, c_int]
     lib.orc_em_admm_batch.restype = c_int
     lib.orc_nlem.argtypes = [F, c_int, c_int, c_int, c_int, c_double, c_double, c_int, c_double,
-                             c_double, c_double, c_int, c_int, c_int, LL, c_ll, D, I, D, D, I, D, c_int, c_int]
+                             c_double, c_double, c_int, c_int, c_int, LL, c_ll, D, I, D, D, I, D, c_int, c_int, I,
+                             D, c_int]
     lib.orc_nlem.restype = c_int
     lib.orc_em_admm_wpen.argtypes = [D, D, c_int, c_int, c_double, c_double, c_double, c_int, D, c_double, c_int,
                                      D, I, D, D]
@@ -172,9 +173,13 @@ def project_set(x, kind, a, b=None, r=0.0):
     return out
 
 
-def em_admm_fast(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, eta=0.999):
+def em_admm_fast(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, eta=0.999, with_margin=False,
+                 restart_every=0, combined=False):
     """Accelerated Algorithm 1 (fast ADMM with restart, Goldstein et al. 2014; accelerated ADMM is
-    the future work Sec. 4 names).  Returns (z, iters_used, r_pri, r_dual, restarts)."""
+    the future work Sec. 4 names).  The restart test compares the z-part mu n ||z - z_hat||^2 of
+    Goldstein's combined residual (combined=True: the whole combined residual); restart_every = k > 0
+    restarts after every k-th iteration instead.  Returns (z, iters_used, r_pri, r_dual, restarts),
+    plus the decision margin min |c / (eta c_prev) - 1| with with_margin."""
     pts, w = _f64(pts), _f64(w)
     if pts.ndim == 1:
         pts = pts[:, None]
@@ -185,12 +190,14 @@ def em_admm_fast(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, eta
     rp = np.zeros(1)
     rd = np.zeros(1)
     z0a = _f64(z0) if z0 is not None else None
+    marg = np.zeros(1)
     rc = _load().orc_em_admm_fast(_dp(pts), _dp(w), n, d, float(lo), float(hi), float(mu), int(iters), _dp(z0a),
-                                  float(tol), int(check_every), float(eta), _dp(z), _ip(used), _dp(rp), _dp(rd),
-                                  _ip(rest))
+                                  float(tol), int(check_every), float(eta), int(restart_every), int(bool(combined)),
+                                  _dp(z), _ip(used), _dp(rp), _dp(rd), _ip(rest), _dp(marg))
     if rc != 0:
         raise MemoryError("oracle em_admm_fast out of memory")
-    return z, int(used[0]), float(rp[0]), float(rd[0]), int(rest[0])
+    res = (z, int(used[0]), float(rp[0]), float(rd[0]), int(rest[0]))
+    return res + (float(marg[0]),) if with_margin else res
 
 
 def em_admm_wpen(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1):
@@ -291,9 +298,13 @@ def irls(pts, w, lo, hi, x0, eps, iters):
     return x, F[:iters]
 
 
-def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nthreads=0, penalty=0):
+def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nthreads=0, penalty=0,
+                  fast=False, extra=False, restart_every=0):
     """Algorithm 1 on a float32 batch [B, n, d] (threads over problems); penalty 1 solves each
-    problem with em_admm_wpen instead.  Returns (z [B,d] float64, iters_used [B], r_pri [B], r_dual [B])."""
+    problem with em_admm_wpen instead, fast=True with em_admm_fast (eta = 0.999, restart_every as
+    there).  Returns
+    (z [B,d] float64, iters_used [B], r_pri [B], r_dual [B]); with extra also the restarts [B]
+    and decision margins [B] of em_admm_fast."""
     pts = np.ascontiguousarray(pts, dtype=np.float32)
     w = np.ascontiguousarray(w, dtype=np.float32)
     B, n, d = pts.shape
@@ -302,19 +313,24 @@ def em_admm_batch(pts, w, lo, hi, mu, iters, z0=None, tol=0.0, check_every=1, nt
     rp = np.zeros(B)
     rd = np.zeros(B)
     z0a = np.ascontiguousarray(z0, dtype=np.float32) if z0 is not None else None
+    rest = np.zeros(B, dtype=np.int32)
+    marg = np.full(B, np.inf)
+    method = 2 if fast else int(penalty)
     rc = _load().orc_em_admm_batch(_fp(pts), _fp(w), B, n, d, float(lo), float(hi), float(mu), int(iters),
                                    _fp(z0a), float(tol), int(check_every), _dp(z), _ip(used), _dp(rp), _dp(rd),
-                                   int(nthreads), int(penalty))
+                                   int(nthreads), method, _ip(rest), _dp(marg), int(restart_every))
     if rc != 0:
         raise MemoryError("oracle em_admm_batch failed")
-    return z, used, rp, rd
+    return (z, used, rp, rd, rest, marg) if extra else (z, used, rp, rd)
 
 
 def nlem(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init_mode=0,
-         weight_mode=0, pixels=None, nthreads=0, penalty=0):
+         weight_mode=0, pixels=None, nthreads=0, penalty=0, fast=False, restart_every=0):
     """NLEM (Sec. 3) on a float32 image; penalty 1 solves each pixel's problem with em_admm_wpen
-    (per-point penalties mu_k = mu w_k).  Returns a dict with out (float64), iters_used,
-    r_pri, r_dual, n (points per problem) and wsum (sum of weights), one entry per processed
+    (per-point penalties mu_k = mu w_k), fast=True with em_admm_fast (eta = 0.999, restart_every as
+    there).  Returns a
+    dict with out (float64), iters_used, r_pri, r_dual, n (points per problem), wsum (sum of
+    weights), restarts and margin (em_admm_fast's; 0 and inf otherwise), one entry per processed
     pixel (all pixels row-major, or the listed linear indices)."""
     img = np.ascontiguousarray(img, dtype=np.float32)
     H, W = img.shape
@@ -330,15 +346,19 @@ def nlem(img, k, S, h, mu, iters, lo=0.0, hi=255.0, tol=0.0, check_every=1, init
     rd = np.zeros(npix)
     nn = np.zeros(npix, dtype=np.int32)
     ws = np.zeros(npix)
+    rest = np.zeros(npix, dtype=np.int32)
+    marg = np.full(npix, np.inf)
     pixp = pix.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if pix is not None else None
+    method = 2 if fast else int(penalty)
     rc = _load().orc_nlem(_fp(img), H, W, int(k), int(S), float(h), float(mu), int(iters), float(lo), float(hi),
                           float(tol), int(check_every), int(init_mode), int(weight_mode), pixp, npix,
-                          _dp(out), _ip(used), _dp(rp), _dp(rd), _ip(nn), _dp(ws), int(nthreads), int(penalty))
+                          _dp(out), _ip(used), _dp(rp), _dp(rd), _ip(nn), _dp(ws), int(nthreads), method,
+                          _ip(rest), _dp(marg), int(restart_every))
     if rc != 0:
         raise MemoryError("oracle nlem failed")
-    res = dict(out=out, iters_used=used, r_pri=rp, r_dual=rd, n=nn, wsum=ws)
+    res = dict(out=out, iters_used=used, r_pri=rp, r_dual=rd, n=nn, wsum=ws, restarts=rest, margin=marg)
     if pixels is None:
-        for key in ("out", "iters_used", "r_pri", "r_dual", "n", "wsum"):
+        for key in ("out", "iters_used", "r_pri", "r_dual", "n", "wsum", "restarts", "margin"):
             res[key] = res[key].reshape(H, W)
     return res
 

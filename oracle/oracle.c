@@ -274,17 +274,27 @@ int orc_em_admm_wpen(const double *pts, const double *w, int n, int d, double lo
 
 /* Algorithm 1 with Nesterov-type momentum and restart (fast ADMM with restart; Goldstein et al.
  * 2014, the variant for objectives that are not strongly convex).  Steps (x, z, y) are those of
- * Algorithm 1, taken at the extrapolated z_hat and y_hat.  After each step the combined residual
- * c = ||y - y_hat||^2 / mu + mu * n * ||z - z_hat||^2 decides: if c < eta * c_prev the momentum
+ * Algorithm 1, taken at the extrapolated z_hat and y_hat.  After each step a residual c decides:
+ * with combined != 0 Goldstein's combined residual c = ||y - y_hat||^2 / mu + mu * n * ||z - z_hat||^2,
+ * with combined == 0 its z-part c = mu * n * ||z - z_hat||^2 (the dual residual of the step).  If
+ * c < eta * c_prev the momentum
  * grows, alpha+ = (1 + sqrt(1 + 4 alpha^2)) / 2, and z_hat, y_hat step beyond the new iterate by
  * (alpha - 1) / alpha+ times its change; otherwise alpha = 1, z_hat and y_hat restart from the
  * previous iterate and c_prev is divided by eta.  With alpha = 1 at the start, the first two
  * iterations equal Algorithm 1's.  The stopping rule and residuals are those of orc_em_admm,
- * evaluated at the step's x, y and z, with z_prev the previous iterate.  *restarts (if not NULL)
- * counts the restarts. */
+ * evaluated at the step's x, y and z, with the step's own z-change z - z_hat in place of
+ * z - z_prev (the same when nothing is extrapolated, z_hat = z_prev; after a restart, a step from
+ * z(t-1) can land next to z(t) while far from the optimum).  *restarts (if not NULL)
+ * counts the restarts.  *margin (if not NULL) is the smallest |c / (eta c_prev) - 1| over the
+ * momentum-or-restart decisions taken with a finite c_prev (+inf if there were none): how close
+ * the run came to deciding the other way.
+ * restart_every = k > 0 replaces the residual test by a fixed period (the fixed restart of
+ * O'Donoghue and Candes 2015): the step after iteration t restarts when t % k == 0 and takes the
+ * momentum otherwise; c is then not consulted (margin stays +inf). */
 int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo, double hi, double mu,
-                     int iters, const double *z0, double tol, int check_every, double eta, double *z,
-                     int *iters_used, double *rpri, double *rdual, int *restarts) {
+                     int iters, const double *z0, double tol, int check_every, double eta, int restart_every,
+                     int combined, double *z, int *iters_used, double *rpri, double *rdual, int *restarts,
+                     double *margin) {
   const size_t nd = (size_t)n * d;
   double *x = (double *)malloc(sizeof(double) * nd);
   double *y = (double *)calloc(nd, sizeof(double));
@@ -305,7 +315,7 @@ int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo
   }
   for (int q = 0; q < d; ++q) zh[q] = zo[q] = z[q];
   if (check_every < 1) check_every = 1;
-  double alpha = 1.0, c_prev = INFINITY, rp = 0.0, rd = 0.0;
+  double alpha = 1.0, c_prev = INFINITY, rp = 0.0, rd = 0.0, marg = INFINITY;
   int t_done = 0, nrest = 0;
   for (int t = 1; t <= iters; ++t) {
     /* Algorithm 1's step at (z_hat, y_hat) */
@@ -338,7 +348,7 @@ int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo
       }
       for (int q = 0; q < d; ++q) {
         zz += z[q] * z[q];
-        dz += (z[q] - zo[q]) * (z[q] - zo[q]);
+        dz += (z[q] - zh[q]) * (z[q] - zh[q]);
       }
       double den_p = sqrt(sx), nzn = sqrt((double)n) * sqrt(zz);
       if (nzn > den_p) den_p = nzn;
@@ -350,8 +360,13 @@ int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo
       if (tol > 0.0 && rp < tol && rd < tol) break;
     }
     /* momentum or restart */
-    const double c = cy / mu + mu * (double)n * cz;
-    if (c < eta * c_prev) {
+    const double c = (combined ? cy / mu : 0.0) + mu * (double)n * cz;
+    if (restart_every <= 0 && isfinite(c_prev)) {
+      const double m = fabs(c / (eta * c_prev) - 1.0);
+      if (m < marg) marg = m;
+    }
+    const int momentum = restart_every > 0 ? (t % restart_every) != 0 : c < eta * c_prev;
+    if (momentum) {
       const double a1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * alpha * alpha));
       const double beta = (alpha - 1.0) / a1;
       for (int q = 0; q < d; ++q) zh[q] = z[q] + beta * (z[q] - zo[q]);
@@ -372,6 +387,7 @@ int orc_em_admm_fast(const double *pts, const double *w, int n, int d, double lo
   if (rpri) *rpri = rp;
   if (rdual) *rdual = rd;
   if (restarts) *restarts = nrest;
+  if (margin) *margin = marg;
   free(x); free(y); free(yh); free(yo); free(r); free(v); free(zh); free(zo);
   return 0;
 }
@@ -578,7 +594,11 @@ typedef struct {
   int *iters_used;
   double *rpri, *rdual;
   int status;
-  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen) */
+  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen);
+                    2: accelerated Algorithm 1 (orc_em_admm_fast, eta = 0.999, the z-part test) */
+  int *restarts;
+  double *margin;
+  int restart_every;   /* orc_em_admm_fast's fixed restart period (0: the residual test) */
 } batch_job;
 
 static void *batch_worker(void *arg) {
@@ -596,16 +616,24 @@ static void *batch_worker(void *arg) {
       for (int q = 0; q < d; ++q) z0[q] = (double)J->z0[(size_t)b * d + q];
       zs = z0;
     }
-    int used = 0;
-    double rp = 0, rd = 0;
-    int rc = J->penalty ? orc_em_admm_wpen(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol,
-                                           J->check_every, J->z + (size_t)b * d, &used, &rp, &rd)
-                        : orc_em_admm(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
-                                      J->z + (size_t)b * d, &used, &rp, &rd);
+    int used = 0, nrest = 0;
+    double rp = 0, rd = 0, marg = INFINITY;
+    int rc;
+    if (J->penalty == 2)
+      rc = orc_em_admm_fast(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every, 0.999,
+                            J->restart_every, 0, J->z + (size_t)b * d, &used, &rp, &rd, &nrest, &marg);
+    else if (J->penalty == 1)
+      rc = orc_em_admm_wpen(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
+                            J->z + (size_t)b * d, &used, &rp, &rd);
+    else
+      rc = orc_em_admm(a, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
+                       J->z + (size_t)b * d, &used, &rp, &rd);
     if (rc != 0) {
       J->status = -1;
       break;
     }
+    if (J->restarts) J->restarts[b] = nrest;
+    if (J->margin) J->margin[b] = marg;
     if (J->iters_used) J->iters_used[b] = used;
     if (J->rpri) J->rpri[b] = rp;
     if (J->rdual) J->rdual[b] = rd;
@@ -625,14 +653,15 @@ int orc_num_cores(void) { return resolve_threads(0); }
 int orc_em_admm_batch(const float *pts, const float *w, long long B, int n, int d, double lo,
                       double hi, double mu, int iters, const float *z0, double tol,
                       int check_every, double *z, int *iters_used, double *rpri,
-                      double *rdual, int nthreads, int penalty) {
+                      double *rdual, int nthreads, int penalty, int *restarts, double *margin,
+                      int restart_every) {
   int T = resolve_threads(nthreads);
   if ((long long)T > B) T = (int)(B > 0 ? B : 1);
   pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)T);
   batch_job *jobs = (batch_job *)malloc(sizeof(batch_job) * (size_t)T);
   for (int i = 0; i < T; ++i) {
     batch_job J = {pts, w, z0, B, n, d, iters, check_every, T, i, lo, hi, mu, tol,
-                   z, iters_used, rpri, rdual, 0, penalty};
+                   z, iters_used, rpri, rdual, 0, penalty, restarts, margin, restart_every};
     jobs[i] = J;
     pthread_create(&th[i], NULL, batch_worker, &jobs[i]);
   }
@@ -687,7 +716,11 @@ typedef struct {
   double *out, *rpri, *rdual, *wsum_out;
   int *iters_used, *n_out;
   int status;
-  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen) */
+  int penalty;   /* 0: Algorithm 1; 1: per-point penalties mu_k = mu w_k (orc_em_admm_wpen);
+                    2: accelerated Algorithm 1 (orc_em_admm_fast, eta = 0.999, the z-part test) */
+  int *restarts;
+  double *margin;
+  int restart_every;   /* orc_em_admm_fast's fixed restart period (0: the residual test) */
 } nlem_job;
 
 /* Patch of g centred at (r, c), reflect-padded, row-major k x k, as double. */
@@ -748,16 +781,24 @@ static void *nlem_worker(void *arg) {
       orc_project_box(pc, d, J->lo, J->hi, z0);
       zs = z0;
     }
-    int used = 0;
-    double rp = 0, rd = 0;
-    int rc = J->penalty ? orc_em_admm_wpen(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol,
-                                           J->check_every, z, &used, &rp, &rd)
-                        : orc_em_admm(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every,
-                                      z, &used, &rp, &rd);
+    int used = 0, nrest = 0;
+    double rp = 0, rd = 0, marg = INFINITY;
+    int rc;
+    if (J->penalty == 2)
+      rc = orc_em_admm_fast(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every, 0.999,
+                            J->restart_every, 0, z, &used, &rp, &rd, &nrest, &marg);
+    else if (J->penalty == 1)
+      rc = orc_em_admm_wpen(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every, z, &used,
+                            &rp, &rd);
+    else
+      rc = orc_em_admm(pts, w, n, d, J->lo, J->hi, J->mu, J->iters, zs, J->tol, J->check_every, z, &used, &rp,
+                       &rd);
     if (rc != 0) {
       J->status = -1;
       break;
     }
+    if (J->restarts) J->restarts[t] = nrest;
+    if (J->margin) J->margin[t] = marg;
     J->out[t] = z[(d - 1) / 2];
     if (J->iters_used) J->iters_used[t] = used;
     if (J->rpri) J->rpri[t] = rp;
@@ -777,7 +818,8 @@ done:
 int orc_nlem(const float *img, int H, int W, int k, int S, double h, double mu, int iters,
              double lo, double hi, double tol, int check_every, int init_mode, int weight_mode,
              const long long *pix, long long npix, double *out, int *iters_used, double *rpri,
-             double *rdual, int *n_out, double *wsum_out, int nthreads, int penalty) {
+             double *rdual, int *n_out, double *wsum_out, int nthreads, int penalty, int *restarts,
+             double *margin, int restart_every) {
   int T = resolve_threads(nthreads);
   long long total = pix ? npix : (long long)H * W;
   if ((long long)T > total) T = (int)(total > 0 ? total : 1);
@@ -785,7 +827,8 @@ int orc_nlem(const float *img, int H, int W, int k, int S, double h, double mu, 
   nlem_job *jobs = (nlem_job *)malloc(sizeof(nlem_job) * (size_t)T);
   for (int i = 0; i < T; ++i) {
     nlem_job J = {img, H, W, k, S, iters, check_every, init_mode, weight_mode, T, i,
-                  h, mu, lo, hi, tol, pix, npix, out, rpri, rdual, wsum_out, iters_used, n_out, 0, penalty};
+                  h, mu, lo, hi, tol, pix, npix, out, rpri, rdual, wsum_out, iters_used, n_out, 0, penalty,
+                  restarts, margin, restart_every};
     jobs[i] = J;
     pthread_create(&th[i], NULL, nlem_worker, &jobs[i]);
   }

@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     PREC_BF16,
     PREC_FP32,
     SOLVER_ADMM,
+    SOLVER_FAST,
     SOLVER_IRLS,
     Context,
     WarmStart,

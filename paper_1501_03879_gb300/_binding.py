@@ -14,6 +14,7 @@ INIT_WEIGHTED_MEAN = 0
 INIT_NOISY_PATCH = 1
 SOLVER_ADMM = 0
 SOLVER_IRLS = 1
+SOLVER_FAST = 2
 LAYOUT_AUTO = 0
 LAYOUT_PIXEL = 1
 LAYOUT_PAIR = 2
@@ -48,7 +49,8 @@ class _Set(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_float), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init", ctypes.c_int), ("fp64_check", ctypes.c_int), ("layout", ctypes.c_int),
-                ("solver", ctypes.c_int), ("irls_eps", ctypes.c_float), ("penalty", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("irls_eps", ctypes.c_float), ("penalty", ctypes.c_int),
+                ("restart_every", ctypes.c_int)]
 
 
 _lib = None
@@ -177,7 +179,7 @@ def _stream(device):
 
 
 def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False,
-             layout=0, solver=None, irls_eps=None, penalty=PENALTY_UNIFORM):
+             layout=0, solver=None, irls_eps=None, penalty=PENALTY_UNIFORM, restart_every=0):
     o = _Options()
     load_library().nlem_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -191,6 +193,7 @@ def _options(tol=0.0, check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEA
     if irls_eps is not None:
         o.irls_eps = float(irls_eps)
     o.penalty = int(penalty)
+    o.restart_every = int(restart_every)
     return o
 
 
@@ -245,9 +248,12 @@ def em_solve(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, out=None, ct
 
 
 def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
-                   fp64_check=False, ctx: Context | None = None, out=None, penalty=PENALTY_UNIFORM):
+                   fp64_check=False, ctx: Context | None = None, out=None, penalty=PENALTY_UNIFORM,
+                   solver=SOLVER_ADMM, restart_every=0):
     """Algorithm 1 on B problems: points [B, n, d], weights [B, n] (float32 CUDA).  penalty:
-    PENALTY_UNIFORM (Algorithm 1) or PENALTY_WEIGHTED (mu_k = rho w_k; d = 49).
+    PENALTY_UNIFORM (Algorithm 1) or PENALTY_WEIGHTED (mu_k = rho w_k; d = 49).  solver SOLVER_FAST:
+    accelerated EM-ADMM (d = 49, n <= 448; restart_every 0 = the combined-residual restart test,
+    k >= 1 = restart after every k-th step).
     Returns dict(x [B,d], iters_used [B] int32, residual [B], obj64/kkt64 [B] float64 if fp64_check)."""
     import torch
     B, n, d = points.shape
@@ -271,7 +277,8 @@ def em_solve_batch(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=Non
     if fp64_check:
         obj = torch.empty(B, dtype=torch.float64, device=dev)
         kkt = torch.empty(B, dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, fp64_check=fp64_check, penalty=penalty)
+    o = _options(tol, check_every, fp64_check=fp64_check, penalty=penalty, solver=solver,
+                 restart_every=restart_every)
     _check(load_library().em_solve_batch(c.handle, _ptr(points), _ptr(weights), B, n, d, _Box(*box), float(rho),
                                          int(iters), _ptr(x0), ctypes.byref(o), _ptr(x), _ptr(used), _ptr(resid),
                                          _ptr(obj), _ptr(kkt), _stream(dev)))
@@ -335,7 +342,8 @@ def _host_ptr(t, dtype, shape, name):
 
 
 def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x0=None, tol=0.0, check_every=1,
-                        chunk=0, ctx: Context | None = None, out=None, device=0, penalty=PENALTY_UNIFORM):
+                        chunk=0, ctx: Context | None = None, out=None, device=0, penalty=PENALTY_UNIFORM,
+                        solver=SOLVER_ADMM, restart_every=0):
     """Algorithm 1 on B problems held in HOST memory: points [B, n, d] and weights [B, n] (CPU float32
     tensors, ideally pinned).  The library copies them in chunks of `chunk` problems (0 = about 1 GiB),
     overlapping the copy of each chunk with the solve of the previous one, and copies the results
@@ -357,7 +365,7 @@ def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x
     resid = res.get("residual")
     if resid is None:
         resid = torch.empty(B, dtype=torch.float32, pin_memory=pin)
-    o = _options(tol, check_every, penalty=penalty)
+    o = _options(tol, check_every, penalty=penalty, solver=solver, restart_every=restart_every)
     _check(load_library().em_solve_batch_host(c.handle, pp, wp, B, n, d, _Box(*box), float(rho), int(iters), x0p,
                                               ctypes.byref(o), int(chunk),
                                               _host_ptr(x, torch.float32, (B, d), "x"),
@@ -369,11 +377,14 @@ def em_solve_batch_host(points, weights, box=(0.0, 255.0), rho=1.0, iters=100, x
 
 def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                  precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, fp64_check=False, ctx: Context | None = None,
-                 out=None, layout=LAYOUT_AUTO, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM):
+                 out=None, layout=LAYOUT_AUTO, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM,
+                 restart_every=0):
     """NLEM (Sec. 3) of a float32 CUDA image [H, W].  Returns dict(out [H,W], iters_used,
     residual[, obj64, kkt64]).  layout: LAYOUT_AUTO, LAYOUT_PIXEL (one pixel per CTA) or
     LAYOUT_PAIR (two adjacent pixels per CTA; patch 7, window <= 21, FP32).  solver: SOLVER_ADMM
-    (Algorithm 1) or SOLVER_IRLS (the surrogate of Eq. 2 with irls_eps, exactly `iters` steps)."""
+    (Algorithm 1), SOLVER_IRLS (the surrogate of Eq. 2 with irls_eps, exactly `iters` steps) or
+    SOLVER_FAST (accelerated EM-ADMM, 7x7 patches, one pixel per CTA; restart_every as for
+    em_solve_batch)."""
     import torch
     H, W = image.shape
     _need(image, torch.float32, (H, W), "image")
@@ -393,7 +404,7 @@ def nlem_denoise(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.
     if fp64_check:
         obj = torch.empty((H, W), dtype=torch.float64, device=dev)
         kkt = torch.empty((H, W), dtype=torch.float64, device=dev)
-    o = _options(tol, check_every, precision, init, fp64_check, layout, solver, irls_eps, penalty)
+    o = _options(tol, check_every, precision, init, fp64_check, layout, solver, irls_eps, penalty, restart_every)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                        int(iters), _Box(*box), ctypes.byref(o), _ptr(o_img), _ptr(used), _ptr(resid),
@@ -443,7 +454,8 @@ def nlem_denoise_color(image, patch=5, window=21, h=200.0, rho=1.0, iters=100, b
 
 def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
                       check_every=1, precision=PREC_FP32, init=INIT_WEIGHTED_MEAN, ctx: Context | None = None,
-                      out=None, iters_used=None, device=0, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM):
+                      out=None, iters_used=None, device=0, solver=SOLVER_ADMM, irls_eps=1e-6, penalty=PENALTY_UNIFORM,
+                      restart_every=0):
     """NLEM on HOST buffers (numpy float32 [H, W] or CPU torch tensor, ideally pinned):
     copies in, denoises and copies out inside the library.  Returns the host output."""
     import numpy as np
@@ -458,7 +470,8 @@ def nlem_denoise_host(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, bo
     c = ctx or _ctx(torch.device("cuda", device))
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, pin_memory=img_t.is_pinned())
-    o = _options(tol, check_every, precision, init, solver=solver, irls_eps=irls_eps, penalty=penalty)
+    o = _options(tol, check_every, precision, init, solver=solver, irls_eps=irls_eps, penalty=penalty,
+                 restart_every=restart_every)
     ip = ctypes.c_void_p(iters_used.data_ptr()) if iters_used is not None else None
     _check(load_library().nlem_denoise_host(c.handle, ctypes.c_void_p(img_t.data_ptr()), H, W, int(patch),
                                             int(window), float(h), float(rho), int(iters), _Box(*box),
@@ -729,9 +742,10 @@ def nlem_ws_labels(image, pixels, feats, rho_grid, patch=7, window=21, h=200.0, 
 
 def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
                     init=INIT_WEIGHTED_MEAN, pixels=None, x0=None, rho_pix=None, z_out=False, ctx: Context | None = None,
-                    out=None, penalty=PENALTY_UNIFORM):
+                    out=None, penalty=PENALTY_UNIFORM, solver=SOLVER_ADMM, restart_every=0):
     """NLEM on a pixel list with optional per-pixel start points / penalties (indexed by
-    linear pixel) and the full solution patches.  Returns dict(out, iters_used, residual[, z])."""
+    linear pixel) and the full solution patches; solver SOLVER_ADMM or SOLVER_FAST.  Returns
+    dict(out, iters_used, residual[, z])."""
     import torch
     H, W = image.shape
     c = ctx or _ctx(image.device)
@@ -753,7 +767,7 @@ def nlem_denoise_ex(image, patch=7, window=21, h=200.0, rho=1.0, iters=100, box=
         if z is None:
             z = torch.zeros((H * W, d), dtype=torch.float32, device=dev)
     n = pixels.numel() if pixels is not None else 0
-    opts = _options(tol, check_every, PREC_FP32, init, penalty=penalty)
+    opts = _options(tol, check_every, PREC_FP32, init, penalty=penalty, solver=solver, restart_every=restart_every)
     ip, pitch = _image(image)
     _check(load_library().nlem_denoise_ex(c.handle, ip, H, W, pitch, int(patch), int(window), float(h), float(rho),
                                           int(iters), _Box(*box), ctypes.byref(opts), _ptr(pixels), n, _ptr(x0),

@@ -55,8 +55,10 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
       return fail(NLEM_ERR_INVALID, "unknown init %d", opt->init);
     if (opt->layout < NLEM_LAYOUT_AUTO || opt->layout > NLEM_LAYOUT_PAIR)
       return fail(NLEM_ERR_INVALID, "unknown layout %d", opt->layout);
-    if (opt->solver != NLEM_SOLVER_ADMM && opt->solver != NLEM_SOLVER_IRLS)
+    if (opt->solver != NLEM_SOLVER_ADMM && opt->solver != NLEM_SOLVER_IRLS && opt->solver != NLEM_SOLVER_FAST)
       return fail(NLEM_ERR_INVALID, "unknown solver %d", opt->solver);
+    if (opt->restart_every < 0)
+      return fail(NLEM_ERR_INVALID, "restart_every must be >= 0 (got %d)", opt->restart_every);
     if (opt->solver == NLEM_SOLVER_IRLS) {
       if (!(opt->irls_eps >= 1e-30f) || !finite(opt->irls_eps))
         return fail(NLEM_ERR_INVALID, "irls_eps must be finite and >= 1e-30 (got %g)", opt->irls_eps);
@@ -66,7 +68,24 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
       return fail(NLEM_ERR_INVALID, "unknown penalty %d", opt->penalty);
     if (opt->penalty == NLEM_PENALTY_WEIGHTED && opt->solver == NLEM_SOLVER_IRLS)
       return fail(NLEM_ERR_INVALID, "per-point penalties belong to EM-ADMM, not IRLS");
+    if (opt->penalty == NLEM_PENALTY_WEIGHTED && opt->solver == NLEM_SOLVER_FAST)
+      return fail(NLEM_ERR_UNSUPPORTED, "the accelerated solver takes one penalty for every point");
   }
+  return NLEM_OK;
+}
+
+// Entry points of standalone problems: EM-ADMM or its accelerated form (IRLS is nlem_denoise's).
+int no_irls(const nlem_options* opt, const char* who) {
+  if (opt && opt->solver == NLEM_SOLVER_IRLS)
+    return fail(NLEM_ERR_INVALID, "%s runs EM-ADMM (plain or accelerated), not IRLS", who);
+  return NLEM_OK;
+}
+
+// The accelerated solver's shapes: d = 49, at most nlemk::fast_capacity() points.
+int fast_shape(const nlem_options* opt, int n, int d) {
+  if (opt && opt->solver == NLEM_SOLVER_FAST && (d != 49 || n > nlemk::fast_capacity()))
+    return fail(NLEM_ERR_UNSUPPORTED, "the accelerated solver is compiled for d = 49 and n <= %d (got n = %d, d = %d)",
+                nlemk::fast_capacity(), n, d);
   return NLEM_OK;
 }
 
@@ -96,6 +115,7 @@ nlemk::SolveParams make_params(nlem_box box, float rho, int iters, const nlem_op
   p.d = d;
   p.solver = opt ? opt->solver : NLEM_SOLVER_ADMM;
   p.eps = opt ? opt->irls_eps : 1e-6f;
+  p.restart_every = opt ? opt->restart_every : 0;
   return p;
 }
 
@@ -124,6 +144,8 @@ void nlem_options_default(nlem_options* opt) {
   opt->layout = NLEM_LAYOUT_AUTO;
   opt->solver = NLEM_SOLVER_ADMM;
   opt->irls_eps = 1e-6f;
+  opt->penalty = NLEM_PENALTY_UNIFORM;
+  opt->restart_every = 0;
 }
 
 const char* nlem_last_error(void) { return g_err.c_str(); }
@@ -194,12 +216,13 @@ int em_solve_batch(nlem_ctx* ctx, const float* points, const float* weights, lon
   NLEM_TRACE("em_solve_batch");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
-  if ((rc = admm_only(opt, "em_solve_batch"))) return rc;
+  if ((rc = no_irls(opt, "em_solve_batch"))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
   if (d < 1 || d > 148) return fail(NLEM_ERR_INVALID, "d must be in [1, 148] (got %d)", d);
   if (B == 0) return NLEM_OK;   // an empty batch may pass NULL buffers
   if (!points || !weights || !x_out) return fail(NLEM_ERR_INVALID, "points, weights and x_out must be non-NULL");
+  if ((rc = fast_shape(opt, n, d))) return rc;
   if (n > nlemk::em_capacity(d))
     return fail(NLEM_ERR_UNSUPPORTED, "n = %d, d = %d exceeds the on-chip solver (max n %d for this d)", n,
                 d, nlemk::em_capacity(d));
@@ -295,7 +318,8 @@ int em_solve_batch_host(nlem_ctx* ctx, const float* points_host, const float* we
   NLEM_TRACE("em_solve_batch_host");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
-  if ((rc = admm_only(opt, "em_solve_batch_host"))) return rc;
+  if ((rc = no_irls(opt, "em_solve_batch_host"))) return rc;
+  if ((rc = fast_shape(opt, n, d))) return rc;
   if (B < 0) return fail(NLEM_ERR_INVALID, "B must be >= 0");
   if (n < 1) return fail(NLEM_ERR_INVALID, "n must be >= 1 (got %d)", n);
   if (d < 1 || d > 148) return fail(NLEM_ERR_INVALID, "d must be in [1, 148] (got %d)", d);
@@ -432,6 +456,10 @@ int nlem_denoise(nlem_ctx* ctx, const float* image, int H, int W, int pitch, int
   L.penalty = opt ? opt->penalty : NLEM_PENALTY_UNIFORM;
   if (L.penalty != NLEM_PENALTY_UNIFORM && (patch != 7 || L.layout == NLEM_LAYOUT_PAIR))
     return fail(NLEM_ERR_UNSUPPORTED, "per-point penalties are compiled for 7x7 patches on the one-pixel layout");
+  if (L.prm.solver == NLEM_SOLVER_FAST &&
+      (patch != 7 || window * window > nlemk::fast_capacity() || L.layout == NLEM_LAYOUT_PAIR))
+    return fail(NLEM_ERR_UNSUPPORTED, "the accelerated solver is compiled for 7x7 patches, windows of at most %d "
+                "points, on the one-pixel layout (got patch %d, window %d)", nlemk::fast_capacity(), patch, window);
   if (opt && opt->precision == NLEM_PREC_BF16) {
     // cross terms on the tensor cores into the weight table, then the solver reads it
     const size_t need = (size_t)H * W * (size_t)window * window;

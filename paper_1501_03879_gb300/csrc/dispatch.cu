@@ -22,6 +22,7 @@ int nlem_capacity(int patch) {
 }
 
 int launch_em_batch(const EmLaunch& L) {
+  if (L.prm.solver == 2) return (L.d == 49 && L.penalty == 0) ? launch_em_fast_d49(L) : -1;
   if (L.penalty == 1) return L.d == 49 ? launch_em_wpen_d49(L) : -1;
   if (L.d == 49) return launch_em_d49(L);
   if (L.d == 25) return launch_em_d25(L);
@@ -31,6 +32,7 @@ int launch_em_batch(const EmLaunch& L) {
 
 int launch_nlem_fp32(const NlemLaunch& L) {
   if (L.prm.solver == 1) return L.layout == 2 ? -1 : launch_nlem_irls(L);   // the pair kernel is ADMM only
+  if (L.prm.solver == 2) return (L.patch == 7 && L.layout != 2 && L.penalty == 0) ? launch_nlem_fast_k7(L) : -1;
   if (L.penalty == 1) return (L.patch == 7 && L.layout != 2) ? launch_nlem_wpen_k7(L) : -1;
   if (L.layout == 2) return launch_nlem_pair_k7(L);
   // windows of more than 256 points (17x17 and up): the pixel-pair kernel; smaller windows run

@@ -94,6 +94,12 @@ int nlem_capacity(int patch);
 // patches on the one-pixel layout); -1 for any other shape.
 int launch_em_wpen_d49(const EmLaunch& L);
 int launch_nlem_wpen_k7(const NlemLaunch& L);
+// Accelerated EM-ADMM (L.prm.solver == 2, fast ADMM with restart; L.prm.restart_every): standalone
+// problems of d = 49 and NLEM with 7x7 patches on the one-pixel layout, up to fast_capacity()
+// points; -1 for any other shape.
+int launch_em_fast_d49(const EmLaunch& L);
+int launch_nlem_fast_k7(const NlemLaunch& L);
+int fast_capacity();
 // Standalone batch over per-coordinate boxes (kind 1: a = lo, b = hi, device [d]) or the ball
 // ||x - a|| <= r (kind 2: a = centre, device [d]); its point capacity for dimension d.
 int launch_em_set(const EmLaunch& L, int kind, const float* a, const float* b, float r);

@@ -6,6 +6,7 @@
 
 #include "admm_core.cuh"
 #include "debug.h"
+#include "fast_core.cuh"
 #include "irls_core.cuh"
 #include "kernels.h"
 
@@ -16,14 +17,16 @@ namespace nlemk {
 // shared-memory point rows, one problem per CTA iteration
 // ------------------------------------------------------------------------------------------
 // PJ: the constraint set (ScalarBox = the box of SolveParams; CoordBoxes, Ball from admm_core.cuh).
-// WPEN: per-point penalties mu_k = mu w_k (admm_iterate).
-template <class C, class PJ = ScalarBox, bool WPEN = false>
+// WPEN: per-point penalties mu_k = mu w_k (admm_iterate).  FAST: accelerated EM-ADMM
+// (admm_fast_iterate, box only; the point rows then hold -a_j and its d-vectors follow the carve).
+template <class C, class PJ = ScalarBox, bool WPEN = false, bool FAST = false>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, long long B, int n,
                 int d, SolveParams prm, const float* __restrict__ x0, float* __restrict__ x_out,
                 int* __restrict__ iters_used, float* __restrict__ resid, double* __restrict__ obj64,
                 double* __restrict__ kkt64, PJ pj = PJ()) {
   constexpr bool kBox = std::is_same<PJ, ScalarBox>::value;
+  static_assert(!FAST || (kBox && !WPEN), "the accelerated solver takes the box and one penalty");
   extern __shared__ float4 smem_raw[];
   Smem<C> sm(reinterpret_cast<float*>(smem_raw));
   const int t = threadIdx.x;
@@ -45,7 +48,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
       const float v = __ldg(P + idx);
       bad |= !isfinite(v);
       const int r = j * C::DP + sg * C::QA + i;
-      if (NLEM_DBG_OK(r, C::SZ_PTS, kDbgPointRow)) sm.pts[r] = v;
+      if (NLEM_DBG_OK(r, C::SZ_PTS, kDbgPointRow)) sm.pts[r] = FAST ? -v : v;
     }
     for (int j = t; j < C::CAP; j += C::NT) {
       float lam = 0.f;
@@ -93,9 +96,12 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
         const int j = pg + p * C::NG;
         wreg[p] = j < n ? __ldg(Wt + j) : 0.f;
       }
-      weighted_mean_start<C, NoExchange, PJ, false>(sm, wreg, n, dd, prm, pj);
+      weighted_mean_start<C, NoExchange, PJ, FAST>(sm, wreg, n, dd, prm, pj);
     }
-    admm_iterate<C, C::G == 2, NoExchange, PJ, WPEN, false>(sm, n, dd, prm, pj);
+    if constexpr (FAST)
+      admm_fast_iterate<C>(sm, FastVec<C>(sm.pts + C::TOTAL), n, dd, prm, prm.restart_every);
+    else
+      admm_iterate<C, C::G == 2, NoExchange, PJ, WPEN, false>(sm, n, dd, prm, pj);
     for (int q = t; q < dd; q += C::NT) {
       const int sg = q / C::Q, i = q - sg * C::Q;
       x_out[(size_t)b * dd + q] = sm.zv[sg * C::QA + i];
@@ -107,7 +113,7 @@ em_batch_kernel(const float* __restrict__ pts_g, const float* __restrict__ w_g, 
     if (kBox && (obj64 || kkt64)) {   // the projected-gradient residual is the box's
       double F, R;
       auto wfun = [&](int j) { return (double)__ldg(Wt + j); };
-      fp64_check<C, decltype(wfun), false>(sm, n, dd, prm, wfun, F, R);
+      fp64_check<C, decltype(wfun), FAST>(sm, n, dd, prm, wfun, F, R);
       if (t == 0) {
         if (obj64) obj64[b] = F;
         if (kkt64) kkt64[b] = R;
@@ -131,14 +137,17 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
 // weights exp(-||P_i-P_j||^2/h^2) -> start point -> EM-ADMM -> centre coordinate.
 // IRLS: the surrogate solver of Eq. 2 in place of EM-ADMM (NLEM-IRLS, the comparison method of
 // Sec. 3).  WPEN: EM-ADMM with per-point penalties mu_k = mu w_k (admm_iterate).  NEG: the point
-// rows hold -a_j (admm_core.cuh).  Ends with a barrier, so the caller may start the next pixel at once.
-template <class C, int K, bool IRLS = false, bool WPEN = false, bool NEG = false>
+// rows hold -a_j (admm_core.cuh).  FAST: accelerated EM-ADMM (admm_fast_iterate, rows of -a_j, its
+// d-vectors after the carve: the launch adds FastVec<C>::BYTES of shared memory).  Ends with a
+// barrier, so the caller may start the next pixel at once.
+template <class C, int K, bool IRLS = false, bool WPEN = false, bool NEG = false, bool FAST = false>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
                            double* __restrict__ obj64, double* __restrict__ kkt64,
                            const float* __restrict__ wtab, const PixelExtra& ex) {
   static_assert(K * K == C::D, "patch size must match the compiled dimension");
+  static_assert(!FAST || (NEG && !IRLS && !WPEN), "the accelerated solver reads rows of -a_j, one penalty");
   SolveParams pp = prm;   // the pixel's own penalty when the caller passes one
   if (ex.rho) {
     pp.mu = ex.rho[pix];
@@ -270,6 +279,8 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   }
   if constexpr (IRLS)
     irls_iterate<C, NEG>(sm, n, C::D, pp);
+  else if constexpr (FAST)
+    admm_fast_iterate<C>(sm, FastVec<C>(sm.pts + C::TOTAL), n, C::D, pp, pp.restart_every);
   else
     admm_iterate<C, false, NoExchange, ScalarBox, WPEN, NEG>(sm, n, C::D, pp);
   if (ex.z_out) {
@@ -304,7 +315,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   __syncthreads();
 }
 
-template <class C, int K, bool IRLS = false, bool WPEN = false>
+template <class C, int K, bool IRLS = false, bool WPEN = false, bool FAST = false>
 __global__ void __launch_bounds__(C::NT, C::MIN_BLOCKS)
 nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float inv_h2, double ih2,
             SolveParams prm, int init_mode, float* __restrict__ out, int* __restrict__ iters_used,
@@ -317,35 +328,38 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const long long pix = pix_list ? (long long)pix_list[it] : it;
     // rows of -a_j for the 7-point EM-ADMM shapes of 7x7 patches, measured 3% faster that way (the
-    // 4-point shape measured 18% slower and the 9x9 one 0.5%, so the others keep rows of a_j)
-    nlem_pixel<C, K, IRLS, WPEN, (C::P >= 7 && C::D == 49 && !IRLS)>(sm, img, H, W, pitch, S, inv_h2, ih2, prm,
-                                                                      init_mode, pix, out, iters_used, resid, obj64,
-                                                                      kkt64, wtab, ex);
+    // 4-point shape measured 18% slower and the 9x9 one 0.5%, so the others keep rows of a_j); the
+    // accelerated solver always reads rows of -a_j
+    constexpr bool kNeg = FAST || (C::P >= 7 && C::D == 49 && !IRLS);
+    nlem_pixel<C, K, IRLS, WPEN, kNeg, FAST>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out,
+                                             iters_used, resid, obj64, kkt64, wtab, ex);
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-template <class C, class PJ = ScalarBox, bool WPEN = false>
+template <class C, class PJ = ScalarBox, bool WPEN = false, bool FAST = false>
 inline int launch_em(const EmLaunch& L, int grid_mult, const PJ& pj = PJ()) {
-  auto kern = em_batch_kernel<C, PJ, WPEN>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+  auto kern = em_batch_kernel<C, PJ, WPEN, FAST>;
+  const size_t smem = C::SMEM_BYTES + (FAST ? FastVec<C>::BYTES : 0);
+  if (smem > 232448) return -1;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   long long grid = L.B;
   long long cap = (long long)L.sm_count * C::MIN_BLOCKS * grid_mult;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, C::NT, C::SMEM_BYTES, L.stream>>>(L.pts, L.w, L.B, L.n, L.d, L.prm, L.x0, L.x_out,
-                                                          L.iters_used, L.resid, L.obj64, L.kkt64, pj);
+  kern<<<(unsigned)grid, C::NT, smem, L.stream>>>(L.pts, L.w, L.B, L.n, L.d, L.prm, L.x0, L.x_out, L.iters_used,
+                                                 L.resid, L.obj64, L.kkt64, pj);
   return (int)cudaGetLastError();
 }
 
-template <class C, int K, bool IRLS = false, bool WPEN = false>
+template <class C, int K, bool IRLS = false, bool WPEN = false, bool FAST = false>
 inline int launch_nlem(const NlemLaunch& L, int grid_mult) {
   if ((L.S + K - 1) * (L.S + K - 1) > C::SZ_WRED) return -1;   // tile must fit its region
-  auto kern = nlem_kernel<C, K, IRLS, WPEN>;
-  const size_t smem = C::SMEM_BYTES;
+  auto kern = nlem_kernel<C, K, IRLS, WPEN, FAST>;
+  const size_t smem = C::SMEM_BYTES + (FAST ? FastVec<C>::BYTES : 0);
   if (smem > 232448) return -1;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;

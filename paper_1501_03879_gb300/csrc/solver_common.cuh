@@ -16,8 +16,9 @@ struct SolveParams {
   float tol;           // <= 0: fixed count
   int check_every;     // residual check period
   int d;               // runtime dimension (used when D == 0)
-  int solver;          // 0 = EM-ADMM (Algorithm 1), 1 = IRLS on the surrogate of Eq. 2
+  int solver;          // 0 = EM-ADMM (Algorithm 1), 1 = IRLS on the surrogate of Eq. 2, 2 = accelerated EM-ADMM
   float eps;           // IRLS smoothing epsilon of Eq. 2
+  int restart_every;   // accelerated EM-ADMM: 0 = restart by the combined-residual test, k > 0 = every k steps
 };
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {

@@ -104,6 +104,8 @@ nlemk::NlemLaunch base_launch(nlem_ctx* ctx, const float* image, int H, int W, i
   L.prm.tol = opt ? opt->tol : 0.f;
   L.prm.check_every = opt ? opt->check_every : 1;
   L.prm.d = patch * patch;
+  L.prm.solver = opt ? opt->solver : NLEM_SOLVER_ADMM;
+  L.prm.restart_every = opt ? opt->restart_every : 0;
   L.init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
   L.penalty = opt ? opt->penalty : NLEM_PENALTY_UNIFORM;
   L.sm_count = ctx->sm_count;
@@ -424,8 +426,10 @@ int nlem_denoise_ex(nlem_ctx* ctx, const float* image, int H, int W, int pitch, 
   if (!out) return wfail(NLEM_ERR_INVALID, "out is NULL");
   if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0 || !(box.lo <= box.hi))
     return wfail(NLEM_ERR_INVALID, "rho > 0, iters >= 0 and lo <= hi are required");
-  if (opt && (opt->check_every < 1 || opt->precision != NLEM_PREC_FP32 || opt->solver != NLEM_SOLVER_ADMM))
-    return wfail(NLEM_ERR_INVALID, "options: check_every >= 1, FP32 precision and the EM-ADMM solver");
+  if (opt && (opt->check_every < 1 || opt->precision != NLEM_PREC_FP32 ||
+              (opt->solver != NLEM_SOLVER_ADMM && opt->solver != NLEM_SOLVER_FAST) || opt->restart_every < 0))
+    return wfail(NLEM_ERR_INVALID, "options: check_every >= 1, FP32 precision, the EM-ADMM solver (plain or "
+                 "accelerated) and restart_every >= 0");
   if (pixels && npix < 0) return wfail(NLEM_ERR_INVALID, "npix must be >= 0");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;

@@ -497,6 +497,51 @@ def test_fast_admm_needs_fewer_iterations_at_large_mu():
     assert np.mean(fast) < 0.75 * np.mean(plain), (np.mean(fast), np.mean(plain))
 
 
+def test_fast_admm_fixed_restart_periods_1_and_2_replay_algorithm_1():
+    """With a fixed restart period the schedule is known in closed form.  A restart sets alpha = 1,
+    and the momentum weight (alpha - 1) / alpha+ is 0 at alpha = 1, so with periods 1 and 2 no step
+    ever extrapolates: period 1 redoes every step once from the previous iterate, so iteration 2m
+    ends at Algorithm 1's iterate m; period 2 ends iteration 2m at Algorithm 1's iterate m + 1.
+    Both hold bit for bit and count one restart per period."""
+    rng = np.random.default_rng(53)
+    pts = rng.uniform(0, 255, (40, 6))
+    w = rng.uniform(0.05, 1, 40)
+    for m in (1, 2, 5, 9):
+        za, *_ = oracle.em_admm(pts, w, 10.0, 240.0, 0.2, m)
+        z1, used, _, _, rest = oracle.em_admm_fast(pts, w, 10.0, 240.0, 0.2, 2 * m, restart_every=1)
+        assert np.array_equal(z1, za) and used == 2 * m and rest == 2 * m
+        za1, *_ = oracle.em_admm(pts, w, 10.0, 240.0, 0.2, m + 1)
+        z2, _, _, _, rest2 = oracle.em_admm_fast(pts, w, 10.0, 240.0, 0.2, 2 * m, restart_every=2)
+        assert np.array_equal(z2, za1) and rest2 == m
+    # period 3 is the first that extrapolates: it leaves Algorithm 1 at iteration 3
+    za, *_ = oracle.em_admm(pts, w, 10.0, 240.0, 0.2, 3)
+    z3, *_ = oracle.em_admm_fast(pts, w, 10.0, 240.0, 0.2, 3, restart_every=3)
+    assert not np.array_equal(z3, za)
+
+
+def test_fast_admm_period_beyond_the_run_never_restarts():
+    """A period longer than the run takes the momentum at every step, as the residual test does
+    when it can never fail (eta so large that c < eta c_prev always holds)."""
+    rng = np.random.default_rng(54)
+    pts = rng.uniform(0, 255, (30, 4))
+    w = rng.uniform(0.1, 1, 30)
+    zk, _, _, _, rk = oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.5, 40, restart_every=41)
+    ze, _, _, _, re_ = oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.5, 40, eta=1e300)
+    assert rk == 0 and re_ == 0 and np.array_equal(zk, ze)
+
+
+def test_fast_admm_decision_margin_limits():
+    """The decision margin (a diagnostic of how near the run came to deciding the other way) is
+    +inf where no decision compares two finite residuals: one iteration, or a fixed period."""
+    rng = np.random.default_rng(55)
+    pts = rng.uniform(0, 255, (20, 3))
+    w = rng.uniform(0.1, 1, 20)
+    assert oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.1, 1, with_margin=True)[5] == np.inf
+    assert oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.1, 30, restart_every=4, with_margin=True)[5] == np.inf
+    m = oracle.em_admm_fast(pts, w, 0.0, 255.0, 0.1, 30, with_margin=True)[5]
+    assert 0.0 <= m < np.inf
+
+
 # ---------------------------------------------------------------------------------------
 # the optimality residual at points that are NOT optimal (reading C7), worked by hand
 # ---------------------------------------------------------------------------------------
