@@ -42,7 +42,9 @@ __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // D_ > 0: compile-time dimension with the tight point layout; D_ == 0: runtime d <= G*Q
 // with a zero-filled full layout.
 // MB_ > 0 sets the CTAs per SM the register budget is sized for (default: 2 for 128 threads).
-template <int D_, int G_, int Q_, int P_, int NW_, int MB_ = 0>
+// PAD_: reduction rows RS float4 apart with RS odd, so that a warp's 16-byte row stores and the
+// column reads fall in distinct bank quads (an even row stride conflicts).
+template <int D_, int G_, int Q_, int P_, int NW_, int MB_ = 0, bool PAD_ = false>
 struct Cfg {
   static constexpr int D = D_, G = G_, Q = Q_, P = P_, NW = NW_;
   static constexpr int NT = NW * 32;
@@ -58,6 +60,7 @@ struct Cfg {
   static constexpr int LPG = 32 / G;                // lanes of a warp that share one slice
   static constexpr int QR = rup4(Q + 2);            // reduction row: Q sums + 2 scalars
   static constexpr int NQR = QR / 4;
+  static constexpr int RS = (PAD_ && NQR % 2 == 0) ? NQR + 1 : NQR;   // reduction row stride (float4)
   static constexpr int COLS = G * NQR;              // float4 columns of a reduction
   static constexpr int VEC = G * QA;                // slice-layout vectors (z, c, ...)
   static constexpr int MIN_BLOCKS = MB_ > 0 ? MB_ : ((NT <= 128) ? 2 : 1);
@@ -75,7 +78,7 @@ struct Cfg {
   static constexpr int OFF_SGV = OFF_CV + VEC;
   static constexpr int OFF_PCV = OFF_SGV + VEC;
   static constexpr int OFF_WRED = OFF_PCV + VEC;
-  static constexpr int SZ_WRED = NW * 32 * QR;
+  static constexpr int SZ_WRED = NW * 32 * RS * 4;
   static constexpr int OFF_CRED = OFF_WRED + SZ_WRED;
   static constexpr int OFF_SCAL = OFF_CRED + NW * COLS * 4;
   static constexpr int TOTAL = OFF_SCAL + 16;
@@ -170,7 +173,7 @@ struct NoExchange {
 // Two-level column reduction of every thread's acc[QR] row over the lanes that share a
 // slice.  Returns, in warp 0, the totals of columns lane and lane+32 (float4 each).
 // Contains one __syncthreads; wred/cred may be reused after the caller's next barrier.
-// Variant for callers that already wrote their row (NQR float4) at wred[(warp*32+lane)*NQR].
+// Variant for callers that already wrote their row (NQR float4) at wred[(warp*32+lane)*RS].
 template <class C, class X = NoExchange>
 __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot0, float4& tot1) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -179,7 +182,7 @@ __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot
   constexpr int CP2 = pow2ceil(C::COLS);
   constexpr int LPC = CP2 >= 32 ? 1 : 32 / CP2;            // reducer lanes per column
   constexpr int PER = LPG / LPC;                           // rows summed per reducer lane
-  const float4* wbase = sm.wred + warp * 32 * C::NQR;
+  const float4* wbase = sm.wred + warp * 32 * C::RS;
 #pragma unroll
   for (int c0 = 0; c0 < C::COLS; c0 += 32) {
     const int col = c0 + (CP2 >= 32 ? lane : (lane % CP2));
@@ -191,8 +194,8 @@ __device__ __forceinline__ void block_reduce_rows(const Smem<C>& sm, float4& tot
 #pragma unroll
       for (int m = 0; m < PER; m += 2) {
         const int l = g * LPG + part * PER + m;
-        s = f4add(s, wbase[l * C::NQR + quad]);
-        if (m + 1 < PER) s1 = f4add(s1, wbase[(l + 1) * C::NQR + quad]);
+        s = f4add(s, wbase[l * C::RS + quad]);
+        if (m + 1 < PER) s1 = f4add(s1, wbase[(l + 1) * C::RS + quad]);
       }
       s = f4add(s, s1);
     }
@@ -222,7 +225,7 @@ template <class C, class X = NoExchange>
 __device__ __forceinline__ void block_reduce(const Smem<C>& sm, const float (&acc)[C::QR],
                                              float4& tot0, float4& tot1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* my = sm.wred + (warp * 32 + lane) * C::NQR;
+  float4* my = sm.wred + (warp * 32 + lane) * C::RS;
 #pragma unroll
   for (int i = 0; i < C::NQR; ++i)
     my[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
@@ -570,7 +573,7 @@ __device__ void admm_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
     // phase 2, one float4 column at a time: sum_k g_k into this lane's reduction row and
     // h = s e - a; only four accumulators are live at once
     {
-      float4* my = sm.wred + (warp * 32 + lane) * C::NQR;
+      float4* my = sm.wred + (warp * 32 + lane) * C::RS;
       const float* abase = sm.pts + pg * C::DP + g * C::QA;
       // two point quads in flight ahead of their use (linear order: quad-major, point-minor)
       float4 a_n1 = load_quad<C>(abase, 0, last);

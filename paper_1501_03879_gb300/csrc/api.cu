@@ -77,7 +77,7 @@ int check_common(nlem_ctx* ctx, nlem_box box, float rho, int iters, const nlem_o
 // Entry points of standalone problems: EM-ADMM or its accelerated form (IRLS is nlem_denoise's).
 int no_irls(const nlem_options* opt, const char* who) {
   if (opt && opt->solver == NLEM_SOLVER_IRLS)
-    return fail(NLEM_ERR_INVALID, "%s runs EM-ADMM (plain or accelerated), not IRLS", who);
+    return fail(NLEM_ERR_INVALID, "%s runs EM-ADMM only (plain or accelerated), not IRLS", who);
   return NLEM_OK;
 }
 

@@ -151,7 +151,7 @@ template <class C>
 __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bool last, const float (&f)[C::P],
                                             float w2, float gs, float2 (&O2)[C::P][C::Q / 2], float (&O1)[C::P]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* my = sm.wred + (warp * 32 + lane) * C::NQR;
+  float4* my = sm.wred + (warp * 32 + lane) * C::RS;
   const float* abase = sm.pts + pg * C::DP + g * C::QA;
   // two point quads in flight ahead of their use (linear order: quad-major, point-minor)
   float4 a_n1 = load_quad<C>(abase, 0, last);
@@ -207,6 +207,42 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
   }
 }
 
+// The first level of the block reduction: each warp sums its own rows per column into cred (one
+// float4 per warp and column); then the CTA barrier.  Warp 0's finalize adds the NW partials of the
+// two slots each of its lanes takes, with no further exchange.
+template <class C>
+__device__ __forceinline__ void fast_reduce_rows(const Smem<C>& sm) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  __syncwarp();
+  constexpr int CP2 = pow2ceil(C::COLS);
+  static_assert(CP2 <= 32 && C::COLS <= 32, "one column per reducer lane group");
+  constexpr int LPC = 32 / CP2;                 // reducer lanes per column
+  constexpr int PER = C::LPG / LPC;             // rows summed per reducer lane
+  const float4* wbase = sm.wred + warp * 32 * C::RS;
+  const int col = lane % CP2, part = lane / CP2;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (col < C::COLS) {
+    const int g = col / C::NQR, quad = col - g * C::NQR;
+    float4 s1 = s;
+#pragma unroll
+    for (int m = 0; m < PER; m += 2) {
+      const int l = g * C::LPG + part * PER + m;
+      s = f4add(s, wbase[l * C::RS + quad]);
+      if (m + 1 < PER) s1 = f4add(s1, wbase[(l + 1) * C::RS + quad]);
+    }
+    s = f4add(s, s1);
+  }
+#pragma unroll
+  for (int o = CP2; o < 32; o <<= 1) {
+    s.x += __shfl_xor_sync(kFull, s.x, o);
+    s.y += __shfl_xor_sync(kFull, s.y, o);
+    s.z += __shfl_xor_sync(kFull, s.z, o);
+    s.w += __shfl_xor_sync(kFull, s.w, o);
+  }
+  if (part == 0 && col < C::COLS) sm.cred[warp * C::COLS + col] = s;
+  __syncthreads();
+}
+
 // Warp 0 state of the momentum / restart rule, identical in every lane.
 struct FastRule {
   float alpha, c_prev;
@@ -239,38 +275,69 @@ __device__ __forceinline__ void fast_zstep(float zh, float A, float inv_n, float
 template <class C>
 __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C>& fv, int d, int it, bool check,
                                               float inv_n, float fn, const SolveParams& prm, int restart_every,
-                                              const float4& t0, const float4& t1, FastRule& R) {
+                                              FastRule& R) {
+  static_assert(C::COLS <= 16, "the finalize gives each lane of warp 0 two slots of one column");
   constexpr float kEta = 0.999f;
   const int lane = threadIdx.x & 31;
+  // the momentum coefficients, formed before the decision that may not need them
+  const float a1 = 0.5f * (1.f + sqrtf(fmaf(4.f * R.alpha, R.alpha, 1.f)));
+  const float beta_m = (R.alpha - 1.f) / a1;
+  // lane l takes slots 2 (l & 1) and 2 (l & 1) + 1 of column l / 2: its totals are the sum of the
+  // NW per-warp partials
+  const int col = lane >> 1, hh = lane & 1;
+  const bool colok = col < C::COLS;
+  const int sg = colok ? col / C::NQR : 0, quad = colok ? col - sg * C::NQR : 0;
+  const bool has = colok && quad < C::NQA;       // the pair lies in the d-vectors
+  const int real = slice_real<C>(sg, d);
+  const int slot0 = 4 * quad + 2 * hh;
+  const int vi = sg * C::QA + slot0;
+  float2 Aa = make_float2(0.f, 0.f), Ab = Aa;
+  if (colok) {
+    const float2* cr = reinterpret_cast<const float2*>(sm.cred) + 2 * col + hh;
+#pragma unroll
+    for (int w = 0; w < C::NW; w += 2) {
+      const float2 va = cr[2 * C::COLS * w];
+      Aa = make_float2(Aa.x + va.x, Aa.y + va.y);
+      if (w + 1 < C::NW) {
+        const float2 vb = cr[2 * C::COLS * (w + 1)];
+        Ab = make_float2(Ab.x + vb.x, Ab.y + vb.y);
+      }
+    }
+  }
+  const float A0 = Aa.x + Ab.x, A1 = Aa.y + Ab.y;
+  float2 zh2 = make_float2(0.f, 0.f), zo2 = zh2, do2 = zh2, go2 = zh2, dl2 = zh2;
+  if (has) {
+    zh2 = *reinterpret_cast<const float2*>(fv.zh + vi);
+    zo2 = *reinterpret_cast<const float2*>(sm.zv + vi);
+    do2 = *reinterpret_cast<const float2*>(fv.dv + vi);
+    go2 = *reinterpret_cast<const float2*>(sm.sgv + vi);
+    dl2 = *reinterpret_cast<const float2*>(fv.dl + vi);
+  }
+  float z[2] = {0.f, 0.f}, D[2] = {0.f, 0.f};
   float p_W2 = 0.f, p_gs = 0.f, p_DD = 0.f, p_eD = 0.f, p_eSw = 0.f, p_rSw = 0.f, p_rr = 0.f, p_zz = 0.f, p_DA = 0.f;
 #pragma unroll
-  for (int k8 = 0; k8 < 8; ++k8) {
-    const int col = lane + 32 * (k8 / 4);
-    if (col >= C::COLS) continue;
-    const int sg = col / C::NQR, quad = col - sg * C::NQR;
-    const int slot = 4 * quad + (k8 % 4);
-    const float A = f4get(k8 < 4 ? t0 : t1, k8 % 4);
-    if (quad < C::NQA && slot < slice_real<C>(sg, d)) {
-      const int vi = sg * C::QA + slot;
-      const float zh = fv.zh[vi];
-      float z, D;
-      fast_zstep(zh, A, inv_n, prm.lo, prm.hi, z, D);
-      p_DD = fmaf(D, D, p_DD);
+  for (int i = 0; i < 2; ++i) {
+    const int slot = slot0 + i;
+    const float A = i ? A1 : A0;
+    if (has && slot < real) {
+      const float zh = i ? zh2.y : zh2.x;
+      fast_zstep(zh, A, inv_n, prm.lo, prm.hi, z[i], D[i]);
+      p_DD = fmaf(D[i], D[i], p_DD);
       if (check) {
-        const float Do = fv.dv[vi];
-        const float Sw = fmaf(fn, Do, -fv.uh[vi] - A);   // sum_k (x_k - r)
-        const float eD = D - Do;
+        const float Do = i ? do2.y : do2.x;
+        const float Sw = fmaf(fn, Do, -fv.uh[vi + i] - A);   // sum_k (x_k - r)
+        const float eD = D[i] - Do;
         const float r = zh - Do;
         p_eD = fmaf(eD, eD, p_eD);
         p_eSw = fmaf(eD, Sw, p_eSw);
         p_rSw = fmaf(r, Sw, p_rSw);
         p_rr = fmaf(r, r, p_rr);
-        p_zz = fmaf(z, z, p_zz);
-        p_DA = fmaf(D, A, p_DA);
+        p_zz = fmaf(z[i], z[i], p_zz);
+        p_DA = fmaf(D[i], A, p_DA);
       }
-    } else if (slot == C::Q) {
+    } else if (colok && slot == C::Q) {
       p_W2 += A;
-    } else if (slot == C::Q + 1) {
+    } else if (colok && slot == C::Q + 1) {
       p_gs += A;
     }
   }
@@ -306,8 +373,7 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   if (!stop) {
     mom = restart_every > 0 ? (it % restart_every) != 0 : cc < kEta * R.c_prev;
     if (mom) {
-      const float a1 = 0.5f * (1.f + sqrtf(fmaf(4.f * R.alpha, R.alpha, 1.f)));
-      beta = (R.alpha - 1.f) / a1;
+      beta = beta_m;
       R.alpha = a1;
       R.c_prev = cc;
     } else {
@@ -317,44 +383,40 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
     }
   }
   const float bp = 1.f + beta;
-  // the next step's vectors, one slot at a time (phantom slots stay zero)
+  // the next step's vectors for the lane's two slots (phantom slots stay zero)
+  if (has) {
+    float zhn[2], zrn[2], cn[2], uhn[2], dln[2], gn[2];
 #pragma unroll
-  for (int k8 = 0; k8 < 8; ++k8) {
-    const int col = lane + 32 * (k8 / 4);
-    if (col >= C::COLS) continue;
-    const int sg = col / C::NQR, quad = col - sg * C::NQR;
-    if (quad >= C::NQA) continue;
-    const int slot = 4 * quad + (k8 % 4);
-    const int vi = sg * C::QA + slot;
-    const float A = f4get(k8 < 4 ? t0 : t1, k8 % 4);
-    float z = 0.f, D = 0.f, zhn = 0.f, zrn = 0.f, cn = 0.f, uhn = 0.f, dln = 0.f;
-    if (slot < slice_real<C>(sg, d)) {
-      const float zh = fv.zh[vi];
-      fast_zstep(zh, A, inv_n, prm.lo, prm.hi, z, D);
-      const float zo = sm.zv[vi], Do = fv.dv[vi], Go = sm.sgv[vi];
-      const float st = fv.dl[vi] - D;                  // z(t) - z(t-1)
-      if (mom) {
-        zhn = fmaf(beta, st, z);
-        cn = fmaf(beta, Do, fmaf(-bp, D, zhn));
-        uhn = fmaf(bp, fmaf(fn, D, -A), -beta * fmaf(fn, Do, -Go));
-        dln = beta * st;
-      } else {
-        zhn = zo;
-        cn = zo - Do;
-        uhn = fmaf(fn, Do, -Go);
-        dln = -st;
+    for (int i = 0; i < 2; ++i) {
+      zhn[i] = zrn[i] = cn[i] = uhn[i] = dln[i] = gn[i] = 0.f;
+      if (slot0 + i < real) {
+        const float A = i ? A1 : A0;
+        const float zo = i ? zo2.y : zo2.x, Do = i ? do2.y : do2.x, Go = i ? go2.y : go2.x;
+        const float st = (i ? dl2.y : dl2.x) - D[i];   // z(t) - z(t-1)
+        if (mom) {
+          zhn[i] = fmaf(beta, st, z[i]);
+          cn[i] = fmaf(beta, Do, fmaf(-bp, D[i], zhn[i]));
+          uhn[i] = fmaf(bp, fmaf(fn, D[i], -A), -beta * fmaf(fn, Do, -Go));
+          dln[i] = beta * st;
+        } else {
+          zhn[i] = zo;
+          cn[i] = zo - Do;
+          uhn[i] = fmaf(fn, Do, -Go);
+          dln[i] = -st;
+        }
+        zrn[i] = zhn[i] - D[i];
+        gn[i] = A;
       }
-      zrn = zhn - D;
     }
-    sm.zv[vi] = z;
+    *reinterpret_cast<float2*>(sm.zv + vi) = make_float2(z[0], z[1]);
     if (!stop) {
-      fv.zh[vi] = zhn;
-      fv.zr[vi] = zrn;
-      sm.cv[vi] = cn;
-      fv.uh[vi] = uhn;
-      fv.dv[vi] = D;
-      fv.dl[vi] = dln;
-      sm.sgv[vi] = A;
+      *reinterpret_cast<float2*>(fv.zh + vi) = make_float2(zhn[0], zhn[1]);
+      *reinterpret_cast<float2*>(fv.zr + vi) = make_float2(zrn[0], zrn[1]);
+      *reinterpret_cast<float2*>(sm.cv + vi) = make_float2(cn[0], cn[1]);
+      *reinterpret_cast<float2*>(fv.uh + vi) = make_float2(uhn[0], uhn[1]);
+      *reinterpret_cast<float2*>(fv.dv + vi) = make_float2(D[0], D[1]);
+      *reinterpret_cast<float2*>(fv.dl + vi) = make_float2(dln[0], dln[1]);
+      *reinterpret_cast<float2*>(sm.sgv + vi) = make_float2(gn[0], gn[1]);
     }
   }
   if (lane == 0) {
@@ -394,9 +456,8 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
   if (g != 0) gs = 0.f;   // each point's ||g_k||^2 counted once, by its slice-0 lane
   const float w2 = check ? fast_check_w2<C>(sm, fv, g, pg, last, f, n, O2, O1) : 0.f;
   fast_phase2<C>(sm, g, pg, last, f, w2, gs, O2, O1);
-  float4 t0, t1;
-  block_reduce_rows<C>(sm, t0, t1);
-  if (t < 32) fast_finalize<C>(sm, fv, d, it, check, inv_n, fn, prm, restart_every, t0, t1, R);
+  fast_reduce_rows<C>(sm);
+  if (t < 32) fast_finalize<C>(sm, fv, d, it, check, inv_n, fn, prm, restart_every, R);
   __syncthreads();
   return sm.scal[0] != 0.f || it >= prm.iters;
 }

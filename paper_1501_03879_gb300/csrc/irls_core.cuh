@@ -93,7 +93,7 @@ __device__ void irls_iterate(const Smem<C>& sm, int n, int d, const SolveParams&
 #pragma unroll
       for (int p = 0; p < C::P; ++p) den += om[p];
       if (g != 0) den = 0.f;
-      float4* my = sm.wred + (warp * 32 + lane) * C::NQR;
+      float4* my = sm.wred + (warp * 32 + lane) * C::RS;
 #pragma unroll
       for (int i = 0; i < C::NQR; ++i) {
         float acc4[4] = {0.f, 0.f, 0.f, 0.f};

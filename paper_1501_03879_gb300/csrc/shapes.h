@@ -26,8 +26,9 @@ using G120_4 = Cfg<0, 4, 30, 4, 8>;
 using G148_2 = Cfg<0, 4, 37, 2, 8>;
 using G148_4 = Cfg<0, 4, 37, 4, 8, 1>;     // 217 KB of shared memory: one CTA per SM
 // accelerated EM-ADMM (two per-point state banks): 4 lanes of 13 slots per point, 7 points per lane,
-// 448 point slots; 182 registers of state per thread, one CTA of 256 threads per SM
-using F49_7 = Cfg<49, 4, 13, 7, 8>;
+// 448 point slots; 182 registers of state per thread, one CTA of 256 threads per SM; padded
+// reduction rows (4 float4 would put every other lane's row store in the same banks)
+using F49_7 = Cfg<49, 4, 13, 7, 8, 0, true>;
 
 int launch_em_d49(const EmLaunch& L);
 int launch_em_d25(const EmLaunch& L);
