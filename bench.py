@@ -9,6 +9,10 @@ One step = one pass over the production workload:
   * a standalone em_solve_batch of 262144 problems, n = 441, d = 49, points uniform on
     [0, 255] with 10% whole-point outliers at 255*Bernoulli(1/2), weights Exp(1), same
     stopping rule.
+Both run the accelerated solver (NLEM_SOLVER_FAST: Algorithm 1's steps with momentum and restart,
+the accelerated ADMM Sec. 4 names as future work), because at rho = 1 Algorithm 1 itself almost
+never reaches the residual within the cap; the `algorithm1` extra row times the same step with
+Algorithm 1 (the pixel-pair kernel and the plain batch kernel) for comparison.
 Every pixel and every standalone problem is one EM solve; `value` is EM solves per second
 over the whole step (inputs resident in HBM), `mpixel_per_s` the NLEM part alone.  `e2e` is the
 same step through the public API with host buffers (nlem_denoise_host, em_solve_batch_host), the
@@ -71,7 +75,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--profile-case", choices=["traffic", "bf16", "features", "irls", "color", "sets"], default=None,
+    p.add_argument("--profile-case", choices=["traffic", "fast", "bf16", "features", "irls", "color", "sets"],
+                   default=None,
                    help="run a small profiling case (no timing output) and exit")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra rows (rho=1e-3, mixed precision, batch, learned warm start)")
@@ -91,10 +96,10 @@ def rank_workload(rank: int, world: int):
     return {"image_seeds": [SEED * 10 + i + 100 * rank for i in range(len(SIGMAS))], "em_seed": SEED + rank}
 
 
-# The NLEM step (patch 7, window 21, FP32) runs the pixel-pair kernel; the standalone batch the
-# one-problem-per-CTA kernel.
-NLEM_KERNEL = "nlem_pair_kernel"
-EM_KERNEL = "em_batch_kernel"
+# The step's kernels: the accelerated instances of the one-problem-per-CTA kernels,
+# nlem_kernel<F49_7, 7, ..., FAST> for the images and em_batch_kernel<F49_7, ..., FAST> for the batch.
+NLEM_KERNEL = "nlem_kernel_fast"
+EM_KERNEL = "em_batch_kernel_fast"
 
 # Counters of the ncu captures summarised in profiles/, each valid only for the sources its kernel
 # was built from (hash of the code of the files below, comments and whitespace ignored); a kernel
@@ -109,12 +114,20 @@ KERNEL_SOURCES = {
                     _CSRC + "shapes.h"],
     "em_batch_kernel": [_CSRC + "admm_core.cuh", _CSRC + "solver_common.cuh", _CSRC + "solve_kernels.cuh",
                         _CSRC + "shapes.h"],
+    "nlem_kernel_fast": [_CSRC + "fast_core.cuh", _CSRC + "admm_core.cuh", _CSRC + "solver_common.cuh",
+                         _CSRC + "solve_kernels.cuh", _CSRC + "shapes.h", _CSRC + "k_fast.cu"],
+    "em_batch_kernel_fast": [_CSRC + "fast_core.cuh", _CSRC + "admm_core.cuh", _CSRC + "solver_common.cuh",
+                             _CSRC + "solve_kernels.cuh", _CSRC + "shapes.h", _CSRC + "k_fast.cu"],
 }
 PROFILED = {
     "nlem_pair_kernel": {"sources": "ca4c4cf06576c924", "traffic": (132864 + 0) * 16, "fma_pipe_pct": 48.10,
                          "issue_pct": 45.77, "smem_wavefront_pct": 41.38},
     "em_batch_kernel": {"sources": "ce399dc74d7e2592", "traffic": (362494976 + 3801856) * 64, "fma_pipe_pct": 40.76,
                         "issue_pct": 34.87, "smem_wavefront_pct": 65.80},
+    "nlem_kernel_fast": {"sources": "f6a2b09472c7987e", "traffic": (141568 + 0) * 16, "fma_pipe_pct": 27.16,
+                         "issue_pct": 28.49, "smem_wavefront_pct": 39.05},
+    "em_batch_kernel_fast": {"sources": "f6a2b09472c7987e", "traffic": (361694208 + 3984640) * 64,
+                             "fma_pipe_pct": 26.32, "issue_pct": 27.79, "smem_wavefront_pct": 38.02},
 }
 
 
@@ -150,7 +163,8 @@ def profile_case(which="traffic"):
     (7x7 patches, 21x21 window).  irls: NLEM-IRLS, 40 steps from the noisy patch, on a 128x128
     image (sigma 20, h = 200, 7x7 patches, 21x21 window).  color: 7x7 colour patches at the 21x21
     window (two-CTA clusters) on a 128x128x3 image, 20 iterations.  sets: 4096 standalone problems
-    of 441 x 49 in a ball of radius 200, rho = 1, 60 iterations."""
+    of 441 x 49 in a ball of radius 200, rho = 1, 60 iterations.  fast: the traffic case with the
+    accelerated solver (the benchmark step's kernels)."""
     import torch
     import synth
     import paper_1501_03879_gb300 as nl
@@ -192,10 +206,12 @@ def profile_case(which="traffic"):
                             solver=nl.SOLVER_IRLS)
         torch.cuda.synchronize()
         return
+    solver = nl.SOLVER_FAST if which == "fast" else nl.SOLVER_ADMM
     g, _ = synth.noisy_image(10011, 128, 128, 20.0)
     gi = torch.from_numpy(g).to(dev)
     for _ in range(2):
-        nl.nlem_denoise(gi, patch=K_PATCH, window=S_WIN, h=200.0, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK)
+        nl.nlem_denoise(gi, patch=K_PATCH, window=S_WIN, h=200.0, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK,
+                        solver=solver)
     B = 4096
     pts = torch.empty((B, EM_N, EM_D), device=dev)
     if not os.path.exists(synth.SYNTH_LIB):
@@ -203,7 +219,7 @@ def profile_case(which="traffic"):
     synth.device_em_points(SEED, B, EM_N, EM_D, pts.data_ptr(), torch.cuda.current_stream().cuda_stream)
     w = torch.from_numpy(synth.em_weights(SEED, np.arange(B), EM_N)).to(dev)
     for _ in range(2):
-        nl.em_solve_batch(pts, w, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK)
+        nl.em_solve_batch(pts, w, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK, solver=solver)
     torch.cuda.synchronize()
 
 
@@ -213,6 +229,8 @@ def profile_case(which="traffic"):
 #   per NLEM pixel once: 3*n*d (distances) + 2*n*d (weighted mean) + 3*n (exp)
 #   per standalone problem once: 2*n*d (weighted mean)
 #   per (problem, IRLS step): 5*n*d + 4*n (x - a, ||.||^2, sum om a; rsqrt, weight, sum om)
+#   accelerated EM-ADMM, per (problem, iteration): 10*n*d + 4*n (five FP32 operations per element,
+#   2 flops each as above), plus 6*n*d on each check iteration (the primal-residual pass)
 # ------------------------------------------------------------------------------------------
 def window_counts(Hh, Ww, S):
     R = (S - 1) // 2
@@ -233,6 +251,22 @@ def irls_flops(n_map, steps, d):
 
 def em_flops(iters, n, d):
     return float(np.sum((8.0 * n * d + 4.0 * n) * iters.astype(np.float64) + 2.0 * n * d))
+
+
+def _checks(iters, m):
+    """Check iterations of a run of `iters` iterations checked every m (and at its last)."""
+    it = np.asarray(iters, dtype=np.float64)
+    return np.ceil(it / m)
+
+
+def fast_nlem_flops(n_map, iters_map, d, m):
+    return float(np.sum((10.0 * n_map * d + 4.0 * n_map) * iters_map + 6.0 * n_map * d * _checks(iters_map, m)
+                        + 5.0 * n_map * d + 3.0 * n_map))
+
+
+def fast_em_flops(iters, n, d, m):
+    it = iters.astype(np.float64)
+    return float(np.sum((10.0 * n * d + 4.0 * n) * it + 6.0 * n * d * _checks(it, m) + 2.0 * n * d))
 
 
 # ------------------------------------------------------------------------------------------
@@ -310,12 +344,12 @@ def cpu_sample_rate(seconds):
     while t_total < seconds:
         pix = rng.choice(H * W, npix, replace=False)
         t0 = time.perf_counter()
-        oracle.nlem(g, K_PATCH, S_WIN, 10 * SIGMAS[1], RHO, CAP, tol=TOL, check_every=CHECK, pixels=pix)
+        oracle.nlem(g, K_PATCH, S_WIN, 10 * SIGMAS[1], RHO, CAP, tol=TOL, check_every=CHECK, pixels=pix, fast=True)
         probs = rng.choice(EM_B, max(npix // 3, 1), replace=False)
         pts = synth.em_points(SEED, probs, EM_N, EM_D)
         w = synth.em_weights(SEED, probs, EM_N)
         t1 = time.perf_counter()
-        oracle.em_admm_batch(pts, w, BOX[0], BOX[1], RHO, CAP, tol=TOL, check_every=CHECK)
+        oracle.em_admm_batch(pts, w, BOX[0], BOX[1], RHO, CAP, tol=TOL, check_every=CHECK, fast=True)
         t2 = time.perf_counter()
         t_total += (t1 - t0) + (t2 - t1)
         total_solves += npix + probs.size
@@ -323,8 +357,9 @@ def cpu_sample_rate(seconds):
         em_done += probs.size
         npix *= 2
     return total_solves / t_total, cores, (f"{pix_done} NLEM pixels of the 512x512 sigma=20 image and {em_done} "
-                                           f"standalone 441x49 problems, rho=1, tol 1e-4 every 10, cap 300, "
-                                           f"{t_total:.1f} s of wall time on {cores} threads")
+                                           f"standalone 441x49 problems, accelerated EM-ADMM (the step's method), "
+                                           f"rho=1, tol 1e-4 every 10, cap 300, {t_total:.1f} s of wall time on "
+                                           f"{cores} threads")
 
 
 def _bounded(run, items, seconds, chunk0=16):
@@ -364,7 +399,7 @@ def oracle_per_config(seconds_each=3.0):
         return (r * Wc + c).reshape(-1)
     g2, _ = synth.noisy_image(SEED * 10 + 1, H, W, SIGMAS[1])
     n, t, _ = _bounded(lambda px: oracle.nlem(g2, K_PATCH, S_WIN, 10 * SIGMAS[1], RHO, CAP, tol=TOL, check_every=CHECK,
-                                              pixels=px)["out"], crop(H, W), seconds_each)
+                                              pixels=px, fast=True)["out"], crop(H, W), seconds_each)
     rows["production_512_crop"] = {"pixels": n, "seconds": t, "pixels_per_s": n / t}
     g3, _ = synth.noisy_image(SEED * 10 + 30, 1024, 1024, 30.0, salt_pepper=0.05)
     px3 = crop(1024, 1024)
@@ -386,7 +421,7 @@ def oracle_per_config(seconds_each=3.0):
 
     def em_chunk(pr):
         return oracle.em_admm_batch(synth.em_points(SEED, pr, EM_N, EM_D), synth.em_weights(SEED, pr, EM_N), BOX[0],
-                                    BOX[1], RHO, CAP, tol=TOL, check_every=CHECK)[0][:, 0]
+                                    BOX[1], RHO, CAP, tol=TOL, check_every=CHECK, fast=True)[0][:, 0]
     n, t, _ = _bounded(em_chunk, probs, seconds_each)
     rows["standalone_4096_subset"] = {"problems": n, "seconds": t, "solves_per_s": n / t}
     return rows
@@ -401,7 +436,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "NLEM 3x512x512 (sigma 10/20/40, k=7, S=21) + em_solve 262144x441x49, rho=1, "
-                                   "tol 1e-4 cap 300", "sample": sample},
+                                   "tol 1e-4 cap 300", "solver": "accelerated EM-ADMM", "sample": sample},
             "cpu_baseline": {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -425,6 +460,35 @@ def _timed(fn, reps=1, warm=1):
         ms = e0.elapsed_time(e1)
         best = ms if best is None else min(best, ms)
     return best, r
+
+
+def extra_algorithm1(nl, ctx, imgs, B):
+    """The benchmark step with Algorithm 1 itself (the pixel-pair kernel for the images, the plain
+    batch kernel for the standalone problems) at the same settings, against the accelerated step:
+    rates, iterations and the share of solves that reached the cap instead of the residual."""
+    import torch
+    import synth
+    dev = imgs[0].device
+    pts = torch.empty((B, EM_N, EM_D), dtype=torch.float32, device=dev)
+    synth.device_em_points(SEED, B, EM_N, EM_D, pts.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+    w = torch.from_numpy(synth.em_weights(SEED, np.arange(B), EM_N)).to(dev)
+    rows = {}
+    for name, solver in (("algorithm1", nl.SOLVER_ADMM), ("accelerated", nl.SOLVER_FAST)):
+        kw = dict(patch=K_PATCH, window=S_WIN, rho=RHO, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx,
+                  solver=solver)
+        ms_n, rn = _timed(lambda: [nl.nlem_denoise(imgs[i], h=10 * sg, **kw) for i, sg in enumerate(SIGMAS)])
+        ms_e, re_ = _timed(lambda: nl.em_solve_batch(pts, w, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK,
+                                                     ctx=ctx, solver=solver))
+        it_n = np.concatenate([r["iters_used"].cpu().numpy().reshape(-1) for r in rn])
+        it_e = re_["iters_used"].cpu().numpy()
+        rows[name] = {"solves_per_s": (len(SIGMAS) * H * W + B) / ((ms_n + ms_e) * 1e-3),
+                      "mpixel_per_s": len(SIGMAS) * H * W / (ms_n * 1e-3) / 1e6, "em_solves_per_s": B / (ms_e * 1e-3),
+                      "nlem_iters_mean": float(it_n.mean()), "nlem_cap_hit": float(np.mean(it_n >= CAP)),
+                      "em_iters_mean": float(it_e.mean()), "em_cap_hit": float(np.mean(it_e >= CAP)),
+                      "nlem_ms": ms_n, "em_ms": ms_e}
+    rows["accelerated_over_algorithm1"] = rows["accelerated"]["solves_per_s"] / rows["algorithm1"]["solves_per_s"]
+    del pts
+    return rows
 
 
 def extra_small_rho(nl, ctx, imgs):
@@ -786,6 +850,7 @@ def run_extras(nl, ctx, imgs, args):
     except (OSError, ValueError):
         pass
     out = {}
+    out["algorithm1"] = extra_algorithm1(nl, ctx, imgs, args.em_batch)
     out["rho_1e-3"] = extra_small_rho(nl, ctx, imgs)
     out["penalty"] = extra_penalty(nl, ctx, imgs)
     out["table1"] = extra_table1(nl, ctx)
@@ -850,12 +915,13 @@ def main():
             if ev is not None:
                 ev["nlem"][i][0].record(stream)
             nl.nlem_denoise(imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=RHO, iters=CAP, box=BOX, tol=TOL,
-                            check_every=CHECK, ctx=ctx, out=outs[i])
+                            check_every=CHECK, ctx=ctx, out=outs[i], solver=nl.SOLVER_FAST)
             if ev is not None:
                 ev["nlem"][i][1].record(stream)
         if ev is not None:
             ev["em"][0].record(stream)
-        nl.em_solve_batch(pts, wts, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK, ctx=ctx, out=em_out)
+        nl.em_solve_batch(pts, wts, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK, ctx=ctx, out=em_out,
+                          solver=nl.SOLVER_FAST)
         if ev is not None:
             ev["em"][1].record(stream)
 
@@ -897,9 +963,9 @@ def main():
 
     # ---- algorithmic work of the last timed step (iteration counts from the outputs) ----
     n_map = window_counts(H, W, S_WIN)
-    nlem_fl = sum(nlem_flops(n_map, o["iters_used"].cpu().numpy().astype(np.float64), EM_D) for o in outs)
+    nlem_fl = sum(fast_nlem_flops(n_map, o["iters_used"].cpu().numpy().astype(np.float64), EM_D, CHECK) for o in outs)
     em_iters = em_out["iters_used"].cpu().numpy()
-    em_fl = em_flops(em_iters, EM_N, EM_D)
+    em_fl = fast_em_flops(em_iters, EM_N, EM_D, CHECK)
     nlem_iters = np.concatenate([o["iters_used"].cpu().numpy().reshape(-1) for o in outs])
     tf_chain, sms = nl.nlem_fp32_peak(ctx)
     sm_mhz_max = clk.get("sm_max_mhz") or 2070.0
@@ -949,7 +1015,7 @@ def main():
             t0 = time.perf_counter()
             with torch.cuda.stream(em_stream):
                 nl.em_solve_batch_host(host_pts, host_w, box=BOX, rho=RHO, iters=CAP, tol=TOL, check_every=CHECK,
-                                       ctx=ctx_em, out=host_em, device=local)
+                                       ctx=ctx_em, out=host_em, device=local, solver=nl.SOLVER_FAST)
             box_out.append(time.perf_counter() - t0)
 
         def e2e_step(record=False):
@@ -962,7 +1028,8 @@ def main():
             th.start()
             for i, sg in enumerate(SIGMAS):
                 nl.nlem_denoise_host(host_imgs[i], patch=K_PATCH, window=S_WIN, h=10 * sg, rho=RHO, iters=CAP,
-                                     box=BOX, tol=TOL, check_every=CHECK, ctx=ctx, out=host_out[i], device=local)
+                                     box=BOX, tol=TOL, check_every=CHECK, ctx=ctx, out=host_out[i], device=local,
+                                     solver=nl.SOLVER_FAST)
             tb = time.perf_counter()
             th.join()
             if not em_t:
@@ -1010,7 +1077,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "production: NLEM 3x512x512 (sigma 10/20/40, 7x7 patches, 21x21 window, "
                                    "h=10 sigma) + em_solve 262144 problems n=441 d=49; rho=1, tol 1e-4 every 10, "
-                                   "cap 300", "em_batch": B, "l2": "flushed between timed steps (512 MB write)"},
+                                   "cap 300", "em_batch": B, "l2": "flushed between timed steps (512 MB write)",
+                       "solver": "accelerated EM-ADMM: Algorithm 1's steps with momentum and restart (Goldstein et "
+                                 "al. 2014; restart when n||z - z^||^2 fails to fall by 0.999)"},
             "mpixel_per_s": mpix, "em_batch_solves_per_s": em_rate,
             "iterations": {"nlem_mean": float(nlem_iters.mean()), "nlem_cap_hit": float(np.mean(nlem_iters >= CAP)),
                            "em_mean": float(em_iters.mean()), "em_cap_hit": float(np.mean(em_iters >= CAP))},
