@@ -272,16 +272,17 @@ __device__ __forceinline__ void fast_zstep(float zh, float A, float inv_n, float
 // that sum_k ||x_k - z||^2 = W2 + 2 (D - D(t-1)) . sum w~ + n ||D - D(t-1)||^2 keeps small terms, with
 // sum_k w~_k = n D(t-1) - sum_k u^_k - G.  The iterate's step s = z(t) - z(t-1) is carried exactly as
 // s = dl - D, dl = z^(t) - z(t-1) being beta s (momentum) or -s (restart) of the step before.
-template <class C>
-__device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C>& fv, int d, int it, bool check,
-                                              float inv_n, float fn, const SolveParams& prm, int restart_every,
-                                              FastRule& R) {
+// CHECK: a check iteration (residuals and the stopping test); the instance without them carries none of
+// their code, which otherwise lengthens the step's critical path.
+template <class C, bool CHECK>
+__device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C>& fv, int d, int it, float inv_n,
+                                              float fn, const SolveParams& prm, int restart_every, FastRule& R) {
   static_assert(C::COLS <= 16, "the finalize gives each lane of warp 0 two slots of one column");
   constexpr float kEta = 0.999f;
   const int lane = threadIdx.x & 31;
   // the momentum coefficients, formed before the decision that may not need them
   const float a1 = 0.5f * (1.f + sqrtf(fmaf(4.f * R.alpha, R.alpha, 1.f)));
-  const float beta_m = (R.alpha - 1.f) / a1;
+  const float beta_m = __fdividef(R.alpha - 1.f, a1);
   // lane l takes slots 2 (l & 1) and 2 (l & 1) + 1 of column l / 2: its totals are the sum of the
   // NW per-warp partials
   const int col = lane >> 1, hh = lane & 1;
@@ -323,7 +324,7 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
       const float zh = i ? zh2.y : zh2.x;
       fast_zstep(zh, A, inv_n, prm.lo, prm.hi, z[i], D[i]);
       p_DD = fmaf(D[i], D[i], p_DD);
-      if (check) {
+      if constexpr (CHECK) {
         const float Do = i ? do2.y : do2.x;
         const float Sw = fmaf(fn, Do, -fv.uh[vi + i] - A);   // sum_k (x_k - r)
         const float eD = D[i] - Do;
@@ -344,7 +345,7 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   p_DD = warp_sum(p_DD);
   const float cc = fn * p_DD;   // the z-part of the combined residual, divided by mu
   bool stop = false;
-  if (check) {
+  if constexpr (CHECK) {
     p_W2 = warp_sum(p_W2);
     p_gs = warp_sum(p_gs);
     p_eD = warp_sum(p_eD);
@@ -457,7 +458,12 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
   const float w2 = check ? fast_check_w2<C>(sm, fv, g, pg, last, f, n, O2, O1) : 0.f;
   fast_phase2<C>(sm, g, pg, last, f, w2, gs, O2, O1);
   fast_reduce_rows<C>(sm);
-  if (t < 32) fast_finalize<C>(sm, fv, d, it, check, inv_n, fn, prm, restart_every, R);
+  if (t < 32) {
+    if (check)
+      fast_finalize<C, true>(sm, fv, d, it, inv_n, fn, prm, restart_every, R);
+    else
+      fast_finalize<C, false>(sm, fv, d, it, inv_n, fn, prm, restart_every, R);
+  }
   __syncthreads();
   return sm.scal[0] != 0.f || it >= prm.iters;
 }
