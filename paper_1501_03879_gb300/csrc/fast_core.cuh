@@ -244,6 +244,9 @@ __device__ __forceinline__ void fast_reduce_rows(const Smem<C>& sm) {
 }
 
 // Warp 0 state of the momentum / restart rule, identical in every lane.
+// Warp 0 state of the momentum / restart rule, identical in every lane.  The countdowns to the next
+// periodic check and the next fixed-period restart (in place of a remainder per iteration) live in
+// shared memory, scal[6] and scal[7] as integers.
 struct FastRule {
   float alpha, c_prev;
   int restarts;
@@ -254,20 +257,13 @@ struct FastRule {
 // to FP32's relative precision even when it is a few ulps of z.
 __device__ __forceinline__ void fast_zstep(float zh, float A, float inv_n, float lo, float hi, float& z, float& D) {
   const float zu = fmaf(-A, inv_n, zh);
-  if (zu < lo) {
-    z = lo;
-    D = zh - lo;
-  } else if (zu > hi) {
-    z = hi;
-    D = zh - hi;
-  } else {
-    z = zu;
-    D = A * inv_n;
-  }
+  z = fminf(fmaxf(zu, lo), hi);
+  D = z == zu ? A * inv_n : zh - z;
 }
 
 // Warp 0, after the block reduction of step `it`: z, the residuals on check iterations, the
-// momentum-or-restart decision and the next step's vectors; publishes p, q and the stop flag.
+// momentum-or-restart decision and the next step's vectors; publishes the stop flag, p, q and the next
+// step's check flag.
 // Phase 2 measured w~_k = x_k - r against r = z^ - D(t-1), a close guess of z (D changes slowly), so
 // that sum_k ||x_k - z||^2 = W2 + 2 (D - D(t-1)) . sum w~ + n ||D - D(t-1)||^2 keeps small terms, with
 // sum_k w~_k = n D(t-1) - sum_k u^_k - G.  The iterate's step s = z(t) - z(t-1) is carried exactly as
@@ -280,8 +276,11 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   static_assert(C::COLS <= 16, "the finalize gives each lane of warp 0 two slots of one column");
   constexpr float kEta = 0.999f;
   const int lane = threadIdx.x & 31;
+  int* si = reinterpret_cast<int*>(sm.scal);
+  const int ccnt = si[6], rcnt = si[7];
   // the momentum coefficients, formed before the decision that may not need them
-  const float a1 = 0.5f * (1.f + sqrtf(fmaf(4.f * R.alpha, R.alpha, 1.f)));
+  const float ua = fmaf(4.f * R.alpha, R.alpha, 1.f);
+  const float a1 = 0.5f * fmaf(ua, rsqrtf(ua), 1.f);   // (1 + sqrt(1 + 4 alpha^2)) / 2
   const float beta_m = __fdividef(R.alpha - 1.f, a1);
   // lane l takes slots 2 (l & 1) and 2 (l & 1) + 1 of column l / 2: its totals are the sum of the
   // NW per-warp partials
@@ -372,7 +371,7 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   bool mom = true;
   float beta = 0.f;
   if (!stop) {
-    mom = restart_every > 0 ? (it % restart_every) != 0 : cc < kEta * R.c_prev;
+    mom = restart_every > 0 ? rcnt != 1 : cc < kEta * R.c_prev;
     if (mom) {
       beta = beta_m;
       R.alpha = a1;
@@ -421,10 +420,12 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
     }
   }
   if (lane == 0) {
-    sm.scal[0] = stop ? 1.f : 0.f;
-    sm.scal[10] = mom ? bp : 0.f;     // p
-    sm.scal[11] = mom ? -beta : 1.f;  // q
-    sm.scal[9] = (float)R.restarts;
+    // the next step's check flag, then one 16-byte store: stop, p, q, check; the countdowns advance
+    const bool chk = it + 1 == prm.iters || (prm.tol > 0.f && ccnt == 1);
+    *reinterpret_cast<float4*>(sm.scal + 12) = make_float4(stop ? 1.f : 0.f, mom ? bp : 0.f, mom ? -beta : 1.f,
+                                                           chk ? 1.f : 0.f);
+    si[6] = ccnt == 1 ? prm.check_every : ccnt - 1;
+    si[7] = rcnt == 1 ? restart_every : rcnt - 1;
   }
 }
 
@@ -437,8 +438,9 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
                                           float2 (&O2)[C::P][C::Q / 2], float (&O1)[C::P], FastRule& R) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
   const bool last = (g == C::G - 1);
-  const bool check = (it == prm.iters) || (prm.tol > 0.f && (it % prm.check_every) == 0);
-  const float p = sm.scal[10], q = sm.scal[11];
+  const float4 pq = *reinterpret_cast<const float4*>(sm.scal + 12);   // stop, p, q, check
+  const bool check = pq.w != 0.f;
+  const float p = pq.y, q = pq.z;
   float s[C::P];
   fast_phase1<C>(sm, g, last, p, q, L2, L1, O2, O1, s);
 #pragma unroll
@@ -465,7 +467,7 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
       fast_finalize<C, false>(sm, fv, d, it, inv_n, fn, prm, restart_every, R);
   }
   __syncthreads();
-  return sm.scal[0] != 0.f || it >= prm.iters;
+  return sm.scal[12] != 0.f || it >= prm.iters;
 }
 
 // Accelerated EM-ADMM from the state set up by the caller, as for admm_iterate: pts (rows of
@@ -501,15 +503,18 @@ __device__ void admm_fast_iterate(const Smem<C>& sm, const FastVec<C>& fv, int n
     fv.uh[i] = 0.f;
     fv.dl[i] = 0.f;
   }
+  // countdowns: iteration t is a periodic check when the check countdown reads 1 as its flag is formed,
+  // and a fixed-period restart when the restart countdown reads 1 in its finalize
+  FastRule R{1.f, __int_as_float(0x7f800000), 0};
   if (t == 0) {
-    sm.scal[0] = 0.f;
+    const bool chk1 = prm.iters == 1 || (prm.tol > 0.f && prm.check_every == 1);
+    int* si = reinterpret_cast<int*>(sm.scal);
+    si[6] = prm.check_every == 1 ? 1 : prm.check_every - 1;
+    si[7] = restart_every;
     sm.scal[3] = 0.f;
-    sm.scal[9] = 0.f;
-    sm.scal[10] = 1.f;
-    sm.scal[11] = 0.f;
+    *reinterpret_cast<float4*>(sm.scal + 12) = make_float4(0.f, 1.f, 0.f, chk1 ? 1.f : 0.f);   // stop, p, q, check
   }
   __syncthreads();
-  FastRule R{1.f, __int_as_float(0x7f800000), 0};
   int it = 0;
   if (prm.iters > 0) {
     for (;;) {
@@ -519,7 +524,10 @@ __device__ void admm_fast_iterate(const Smem<C>& sm, const FastVec<C>& fv, int n
       if (fast_step<C>(sm, fv, n, d, it, prm, restart_every, inv_n, fn, hB, hB1, hA, hA1, R)) break;
     }
   }
-  if (t == 0) sm.scal[2] = (float)it;
+  if (t == 0) {
+    sm.scal[2] = (float)it;
+    sm.scal[9] = (float)R.restarts;
+  }
   __syncthreads();
 }
 
