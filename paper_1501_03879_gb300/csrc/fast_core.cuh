@@ -145,6 +145,15 @@ __device__ __forceinline__ float fast_check_w2(const Smem<C>& sm, const FastVec<
   return ww2.x + ww2.y + ww1;
 }
 
+// One quad of a point row for phase 2.  A last quad holding a single slot (Q = 4m + 1) is read as one float:
+// a lane then reads 4Q + 4 bytes of its row instead of 4Q + 12, which cuts phase 2's shared-memory
+// wavefronts by 3 of 16 per point.
+template <class C>
+__device__ __forceinline__ float4 load_row_quad(const float* row, int i, bool last) {
+  if (C::Q % 4 == 1 && i == C::NQA - 1) return make_float4((C::D > 0 && last && 4 * i >= C::QL) ? 0.f : row[4 * i], 0.f, 0.f, 0.f);
+  return load_quad<C>(row, i, last);
+}
+
 // Phase 2: from e (in O) and the factors f: the column sums of g = f e (plus W2 and sum ||g||^2 in
 // the two slots after them) into this lane's reduction row, and h = f e - a back into O.
 template <class C>
@@ -154,8 +163,7 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
   float4* my = sm.wred + (warp * 32 + lane) * C::RS;
   const float* abase = sm.pts + pg * C::DP + g * C::QA;
   // two point quads in flight ahead of their use (linear order: quad-major, point-minor)
-  float4 a_n1 = load_quad<C>(abase, 0, last);
-  float4 a_n2 = C::P > 1 ? load_quad<C>(abase + C::NG * C::DP, 0, last) : load_quad<C>(abase, 1, last);
+
 #pragma unroll
   for (int i = 0; i < C::NQR; ++i) {
     float acc4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -164,13 +172,7 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
       float acc1 = 0.f;
 #pragma unroll
       for (int k = 0; k < C::P; ++k) {
-        const float4 a4 = a_n1;
-        a_n1 = a_n2;
-        {
-          const int lin = i * C::P + k + 2;
-          const int ni = lin / C::P, np = lin % C::P;
-          if (ni < C::NQA) a_n2 = load_quad<C>(abase + np * C::NG * C::DP, ni, last);
-        }
+        const float4 a4 = load_row_quad<C>(abase + k * C::NG * C::DP, i, last);
         const float2 f2 = make_float2(f[k], f[k]);
 #pragma unroll
         for (int jh = 0; jh < 2; ++jh) {
