@@ -162,7 +162,6 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* my = sm.wred + (warp * 32 + lane) * C::RS;
   const float* abase = sm.pts + pg * C::DP + g * C::QA;
-  // two point quads in flight ahead of their use (linear order: quad-major, point-minor)
 
 #pragma unroll
   for (int i = 0; i < C::NQR; ++i) {
