@@ -41,7 +41,7 @@ __device__ __forceinline__ bool dbg_ok(long long index, long long limit, int sit
 }
 #define NLEM_DBG_OK(index, limit, site) ::nlemk::dbg_ok((long long)(index), (long long)(limit), (site))
 #else
-#define NLEM_DBG_OK(index, limit, site) true
+#define NLEM_DBG_OK(index, limit, site) ((void)(index), (void)(limit), true)
 #endif
 
 }  // namespace nlemk

@@ -154,13 +154,14 @@ __device__ __forceinline__ float4 load_row_quad(const float* row, int i, bool la
   return load_quad<C>(row, i, last);
 }
 
-// Phase 2: from e (in O) and the factors f: the column sums of g = f e (plus W2 and sum ||g||^2 in
-// the two slots after them) into this lane's reduction row, and h = f e - a back into O.
+// Phase 2: from e (in O) and the factors f: h = f e - a back into O, and the first level of the block
+// reduction.  Each quad's column sums of g = f e over the lane's points (plus W2 and sum ||g||^2 in the
+// two slots after the last column) are summed over the slice's 8 lanes by shuffles, and the warp's
+// partial goes to cred, one float4 per warp and column; warp 0's finalize adds the warps' partials.
 template <class C>
 __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bool last, const float (&f)[C::P],
                                             float w2, float gs, float2 (&O2)[C::P][C::Q / 2], float (&O1)[C::P]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* my = sm.wred + (warp * 32 + lane) * C::RS;
   const float* abase = sm.pts + pg * C::DP + g * C::QA;
 
 #pragma unroll
@@ -204,44 +205,20 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
       if (4 * i + c == C::Q) acc4[c] = w2;
       if (4 * i + c == C::Q + 1) acc4[c] = gs;
     }
-    my[i] = make_float4(acc4[0], acc4[1], acc4[2], acc4[3]);
-  }
-}
-
-// The first level of the block reduction: each warp sums its own rows per column into cred (one
-// float4 per warp and column); then the CTA barrier.  Warp 0's finalize adds the NW partials of the
-// two slots each of its lanes takes, with no further exchange.
-template <class C>
-__device__ __forceinline__ void fast_reduce_rows(const Smem<C>& sm) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  __syncwarp();
-  constexpr int CP2 = pow2ceil(C::COLS);
-  static_assert(CP2 <= 32 && C::COLS <= 32, "one column per reducer lane group");
-  constexpr int LPC = 32 / CP2;                 // reducer lanes per column
-  constexpr int PER = C::LPG / LPC;             // rows summed per reducer lane
-  const float4* wbase = sm.wred + warp * 32 * C::RS;
-  const int col = lane % CP2, part = lane / CP2;
-  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (col < C::COLS) {
-    const int g = col / C::NQR, quad = col - g * C::NQR;
-    float4 s1 = s;
-#pragma unroll
-    for (int m = 0; m < PER; m += 2) {
-      const int l = g * C::LPG + part * PER + m;
-      s = f4add(s, wbase[l * C::RS + quad]);
-      if (m + 1 < PER) s1 = f4add(s1, wbase[(l + 1) * C::RS + quad]);
+    {
+      // sum over the slice's LPG = 8 lanes, reduce-scattered: after xor 4 a lane keeps two of the four
+      // values, after xor 2 one, and xor 1 completes it in both lanes of a pair
+      static_assert(C::LPG == 8, "the fused reduction takes 8 lanes per slice");
+      const bool b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
+      const float s0 = b2 ? acc4[0] : acc4[2], s1 = b2 ? acc4[1] : acc4[3];
+      const float k0 = (b2 ? acc4[2] : acc4[0]) + __shfl_xor_sync(kFull, s0, 4);
+      const float k1 = (b2 ? acc4[3] : acc4[1]) + __shfl_xor_sync(kFull, s1, 4);
+      float k = (b1 ? k1 : k0) + __shfl_xor_sync(kFull, b1 ? k0 : k1, 2);
+      k += __shfl_xor_sync(kFull, k, 1);
+      if ((lane & 1) == 0)
+        reinterpret_cast<float*>(sm.cred)[(warp * C::COLS + g * C::NQR + i) * 4 + (b2 ? 2 : 0) + (b1 ? 1 : 0)] = k;
     }
-    s = f4add(s, s1);
   }
-#pragma unroll
-  for (int o = CP2; o < 32; o <<= 1) {
-    s.x += __shfl_xor_sync(kFull, s.x, o);
-    s.y += __shfl_xor_sync(kFull, s.y, o);
-    s.z += __shfl_xor_sync(kFull, s.z, o);
-    s.w += __shfl_xor_sync(kFull, s.w, o);
-  }
-  if (part == 0 && col < C::COLS) sm.cred[warp * C::COLS + col] = s;
-  __syncthreads();
 }
 
 // Warp 0 state of the momentum / restart rule, identical in every lane.
@@ -460,7 +437,7 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
   if (g != 0) gs = 0.f;   // each point's ||g_k||^2 counted once, by its slice-0 lane
   const float w2 = check ? fast_check_w2<C>(sm, fv, g, pg, last, f, n, O2, O1) : 0.f;
   fast_phase2<C>(sm, g, pg, last, f, w2, gs, O2, O1);
-  fast_reduce_rows<C>(sm);
+  __syncthreads();
   if (t < 32) {
     if (check)
       fast_finalize<C, true>(sm, fv, d, it, inv_n, fn, prm, restart_every, R);
