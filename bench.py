@@ -599,10 +599,10 @@ def extra_mixed_precision(nl, ctx, peaks):
 
 def extra_batch(nl, ctx, with_rho1=True):
     """64 images of uneven sizes (sides 128..1024, 22 M pixels), patch 5 or 7, window 11..21, in
-    one persistent graph-captured launch with the autotuned shape; tol 1e-4, cap 300, at rho = 1
-    (the batched workload's penalty: nearly every pixel runs to the cap, about a minute per pass;
-    skipped by --quick) and at rho = 1e-3.  The algorithmic work counts each pixel's own window
-    size and iterations."""
+    one persistent graph-captured launch with the autotuned shape; tol 1e-4, cap 300.  Algorithm 1
+    at rho = 1 (the batched workload's penalty: nearly every pixel runs to the cap, about a minute per
+    pass) and at rho = 1e-3, and the accelerated solver at rho = 1 (rows at rho = 1 skipped by
+    --quick).  The algorithmic work counts each pixel's own window size and iterations."""
     import torch
     import synth
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -613,14 +613,21 @@ def extra_batch(nl, ctx, with_rho1=True):
     tf_chain, sms = nl.nlem_fp32_peak(ctx)
     peak = sms * 128 * 2 * 2070e6 / 1e12
     rows = {}
-    for rho in ((1.0, 1e-3) if with_rho1 else (1e-3,)):
-        kw = dict(rho=rho, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx)
+    cases = ([(1.0, False)] if with_rho1 else []) + [(1e-3, False)] + ([(1.0, True)] if with_rho1 else [])
+    for rho, fast in cases:
+        kw = dict(rho=rho, iters=CAP, box=BOX, tol=TOL, check_every=CHECK, ctx=ctx,
+                  solver=nl.SOLVER_FAST if fast else nl.SOLVER_ADMM)
         outs = nl.nlem_denoise_batch(ims, *args_, **kw)          # first call: autotune + capture
         ms, outs = _timed(lambda: nl.nlem_denoise_batch(ims, *args_, outs=outs, **kw), warm=0)
         its = [o["iters_used"].cpu().numpy().astype(np.float64) for o in outs]
-        fl = sum(nlem_flops(window_counts(s.H, s.W, s.window), it, s.patch * s.patch) for s, it in zip(specs, its))
+        if fast:
+            fl = sum(fast_nlem_flops(window_counts(s.H, s.W, s.window), it, s.patch * s.patch, CHECK)
+                     for s, it in zip(specs, its))
+        else:
+            fl = sum(nlem_flops(window_counts(s.H, s.W, s.window), it, s.patch * s.patch) for s, it in zip(specs, its))
         ita = np.concatenate([i.reshape(-1) for i in its])
-        rows[str(rho)] = {"mpixel_per_s": npx / (ms * 1e-3) / 1e6, "solves_per_s": npx / (ms * 1e-3),
+        rows[str(rho) + ("_accelerated" if fast else "")] = {
+                          "mpixel_per_s": npx / (ms * 1e-3) / 1e6, "solves_per_s": npx / (ms * 1e-3),
                           "iters_mean": float(ita.mean()), "cap_hit": float(np.mean(ita >= CAP)), "ms": ms,
                           "tflops": fl / (ms * 1e-3) / 1e12, "frac": fl / (ms * 1e-3) / 1e12 / peak,
                           "launch": nl.nlem_batch_config(ctx)}

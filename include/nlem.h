@@ -98,8 +98,8 @@ typedef struct {
                          extrapolation).  Compiled for em_solve_batch (and em_solve_batch_host)
                          with d = 49 and n <= 448, and for nlem_denoise, nlem_denoise_host and
                          nlem_denoise_ex with 7x7 patches and windows of at most 448 points on the
-                         one-pixel layout (AUTO takes it; PAIR is -5); -5 elsewhere and with
-                         per-point penalties */
+                         one-pixel layout (AUTO takes it; PAIR is -5), and for nlem_denoise_batch
+                         (5x5 and 7x7 patches); -5 elsewhere and with per-point penalties */
 } nlem_options;
 
 void nlem_options_default(nlem_options* opt);
@@ -283,7 +283,9 @@ typedef struct {
  * (keyed by SM count, patch set, largest window and stopping mode); that first call runs a few
  * timed trials on a sample of the batch and synchronizes `stream`.
  * rho, iters, box and opt apply to every image; opt->precision must be FP32 and
- * opt->fp64_check is ignored.
+ * opt->fp64_check is ignored.  opt->solver may be NLEM_SOLVER_FAST: the accelerated solver (see
+ * nlem_options.restart_every) on its own shapes, one CTA of 256 threads per SM (ctas_per_sm of
+ * nlem_batch_force_config does not apply to it); IRLS is -1.
  * Errors: -1 on an invalid descriptor (as nlem_denoise), -5 for patch sizes other than 5 and 7
  * or windows whose point count exceeds the batched kernel, -3 if the workspace cannot grow.
  */

@@ -491,10 +491,12 @@ def nlem_fp32_peak(ctx: Context | None = None):
 
 
 def nlem_denoise_batch(images, patches, windows, hs, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0, check_every=1,
-                       init=INIT_WEIGHTED_MEAN, ctx: Context | None = None, outs=None):
+                       init=INIT_WEIGHTED_MEAN, ctx: Context | None = None, outs=None, solver=SOLVER_ADMM,
+                       restart_every=0):
     """NLEM on a list of float32 CUDA images of uneven sizes in one persistent launch
     (CUDA-graph replayed).  patches, windows, hs: per-image patch size, window size and h.
-    Returns a list of dicts (out, iters_used, residual), one per image."""
+    solver: SOLVER_ADMM (Algorithm 1) or SOLVER_FAST (accelerated EM-ADMM; restart_every as for
+    em_solve_batch).  Returns a list of dicts (out, iters_used, residual), one per image."""
     import torch
     n = len(images)
     if not (len(patches) == len(windows) == len(hs) == n):
@@ -517,7 +519,7 @@ def nlem_denoise_batch(images, patches, windows, hs, rho=1.0, iters=100, box=(0.
         d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
         d.H, d.W, d.pitch = H, W, pitch
         d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
-    o = _options(tol, check_every, PREC_FP32, init)
+    o = _options(tol, check_every, PREC_FP32, init, solver=solver, restart_every=restart_every)
     _check(load_library().nlem_denoise_batch(c.handle, descs, n, float(rho), int(iters), _Box(*box), ctypes.byref(o),
                                              _stream(dev)))
     return outs

@@ -708,6 +708,7 @@ int autotune_batch(nlem_ctx* ctx, nlemk::BatchLaunch L, const std::string& key, 
   for (int v = 0; v < nlemk::kBatchVariants; ++v) {
     for (int f : fetches) {
       for (int c : ctas) {
+        if (L.prm.solver == NLEM_SOLVER_FAST && c != 1) continue;   // the accelerated shapes fill an SM
         L.cfg = nlemk::BatchConfig{v, f, c};
         for (int rep = warmed ? 0 : -1; rep < 1; ++rep) {   // one untimed warm-up run at first
           cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), stream);
@@ -752,7 +753,7 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
   NLEM_TRACE("nlem_denoise_batch");
   int rc = check_common(ctx, box, rho, iters, opt);
   if (rc) return rc;
-  if ((rc = admm_only(opt, "nlem_denoise_batch"))) return rc;
+  if ((rc = no_irls(opt, "nlem_denoise_batch"))) return rc;
   if ((rc = uniform_penalty_only(opt, "nlem_denoise_batch"))) return rc;
   if (count < 0) return fail(NLEM_ERR_INVALID, "count must be >= 0");
   if (count == 0) return NLEM_OK;
@@ -839,8 +840,8 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
     L.sm_count = ctx->sm_count;
     L.stream = s;
     char key[160];
-    std::snprintf(key, sizeof(key), "sm%d/patches%d/S%d/tol%d/it%d/init%d", ctx->sm_count, mask, maxS,
-                  prm.tol > 0.f ? 1 : 0, iters, init_mode);
+    std::snprintf(key, sizeof(key), "sm%d/patches%d/S%d/tol%d/it%d/init%d/solver%d", ctx->sm_count, mask, maxS,
+                  prm.tol > 0.f ? 1 : 0, iters, init_mode, prm.solver);
     nlemk::BatchConfig cfg{};
     if (ctx->forced.variant >= 0) {
       cfg = ctx->forced;
@@ -878,7 +879,8 @@ int nlem_denoise_batch(nlem_ctx* ctx, const nlem_image_desc* images, int count, 
     ctx->have_plan = true;
     char desc[256];
     std::snprintf(desc, sizeof(desc), "%s; fetch=%d items; %d CTA/SM; %lld items; key %s",
-                  nlemk::batch_variant_name(cfg.variant), cfg.fetch, cfg.ctas_per_sm, total, key);
+                  nlemk::batch_variant_name(cfg.variant, prm.solver), cfg.fetch,
+                  prm.solver == NLEM_SOLVER_FAST ? 1 : cfg.ctas_per_sm, total, key);
     ctx->last_cfg = desc;
   }
   cudaError_t e = cudaGraphLaunch(ctx->plan.exec, s);

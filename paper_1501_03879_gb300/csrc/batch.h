@@ -43,6 +43,6 @@ constexpr int kBatchVariants = 2;
 int launch_batch(const BatchLaunch& L);          // cudaError_t, or -1 for an unknown variant
 int batch_max_points(int patch, int variant);    // 0 when the patch size is not compiled
 int batch_tile_fits(int patch, int window);
-const char* batch_variant_name(int v);
+const char* batch_variant_name(int v, int solver);   // solver: SolveParams::solver (2 = accelerated)
 
 }  // namespace nlemk

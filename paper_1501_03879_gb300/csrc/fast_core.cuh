@@ -156,7 +156,7 @@ __device__ __forceinline__ float4 load_row_quad(const float* row, int i, bool la
 
 // Phase 2: from e (in O) and the factors f: h = f e - a back into O, and the first level of the block
 // reduction.  Each quad's column sums of g = f e over the lane's points (plus W2 and sum ||g||^2 in the
-// two slots after the last column) are summed over the slice's 8 lanes by shuffles, and the warp's
+// two slots after the last column) are summed over the slice's lanes by shuffles, and the warp's
 // partial goes to cred, one float4 per warp and column; warp 0's finalize adds the warps' partials.
 template <class C>
 __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bool last, const float (&f)[C::P],
@@ -206,16 +206,19 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
       if (4 * i + c == C::Q + 1) acc4[c] = gs;
     }
     {
-      // sum over the slice's LPG = 8 lanes, reduce-scattered: after xor 4 a lane keeps two of the four
-      // values, after xor 2 one, and xor 1 completes it in both lanes of a pair
-      static_assert(C::LPG == 8, "the fused reduction takes 8 lanes per slice");
-      const bool b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
+      // sum over the slice's LPG lanes (8 or 16, consecutive), reduce-scattered: after xor LPG/2 a lane
+      // keeps two of the four values, after xor LPG/4 one, and the remaining levels complete it in every
+      // lane of a group of LPG/4
+      static_assert(C::LPG == 8 || C::LPG == 16, "the fused reduction takes 8 or 16 lanes per slice");
+      constexpr int H1 = C::LPG / 2, H2 = C::LPG / 4;
+      const bool b2 = (lane & H1) != 0, b1 = (lane & H2) != 0;
       const float s0 = b2 ? acc4[0] : acc4[2], s1 = b2 ? acc4[1] : acc4[3];
-      const float k0 = (b2 ? acc4[2] : acc4[0]) + __shfl_xor_sync(kFull, s0, 4);
-      const float k1 = (b2 ? acc4[3] : acc4[1]) + __shfl_xor_sync(kFull, s1, 4);
-      float k = (b1 ? k1 : k0) + __shfl_xor_sync(kFull, b1 ? k0 : k1, 2);
-      k += __shfl_xor_sync(kFull, k, 1);
-      if ((lane & 1) == 0)
+      const float k0 = (b2 ? acc4[2] : acc4[0]) + __shfl_xor_sync(kFull, s0, H1);
+      const float k1 = (b2 ? acc4[3] : acc4[1]) + __shfl_xor_sync(kFull, s1, H1);
+      float k = (b1 ? k1 : k0) + __shfl_xor_sync(kFull, b1 ? k0 : k1, H2);
+#pragma unroll
+      for (int o = H2 / 2; o >= 1; o >>= 1) k += __shfl_xor_sync(kFull, k, o);
+      if ((lane & (H2 - 1)) == 0)
         reinterpret_cast<float*>(sm.cred)[(warp * C::COLS + g * C::NQR + i) * 4 + (b2 ? 2 : 0) + (b1 ? 1 : 0)] = k;
     }
   }

@@ -29,6 +29,12 @@ using G148_4 = Cfg<0, 4, 37, 4, 8, 1>;     // 217 KB of shared memory: one CTA p
 // 448 point slots; 182 registers of state per thread, one CTA of 256 threads per SM; padded
 // reduction rows (4 float4 would put every other lane's row store in the same banks)
 using F49_7 = Cfg<49, 4, 13, 7, 8, 0, true>;
+// the same for the batched launch: fewer point slots for small windows, and 5x5 patches (2 lanes of 13
+// slots per point)
+using F49_2 = Cfg<49, 4, 13, 2, 8, 0, true>;
+using F49_4 = Cfg<49, 4, 13, 4, 8, 0, true>;
+using F25_2 = Cfg<25, 2, 13, 2, 8, 0, true>;
+using F25_4 = Cfg<25, 2, 13, 4, 8, 0, true>;
 
 int launch_em_d49(const EmLaunch& L);
 int launch_em_d25(const EmLaunch& L);

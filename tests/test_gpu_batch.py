@@ -110,6 +110,59 @@ def test_batch_uneven_64_images_sampled(nl):
         assert rel_err(got, ref["out"]).max() <= TOL
 
 
+@pytest.mark.parametrize("forced", [None, 0, 1])
+def test_batch_accelerated_fixed_period_every_pixel(nl, forced):
+    """The accelerated solver in the persistent launch, on a fixed restart period (its schedule does
+    not depend on rounding): every pixel of the seven uneven images against the oracle's
+    em_admm_fast, with the autotuner's shape and with each variant pinned."""
+    specs = _specs()
+    imgs_h = [synth.noisy_image(3500 + i, H, W, s)[0] for i, (H, W, s, k, S) in enumerate(specs)]
+    imgs = [torch.from_numpy(g).to(DEV) for g in imgs_h]
+    ctx = nl.Context(0)
+    if forced is not None:
+        nl.nlem_batch_force_config(forced, fetch=4, ctas_per_sm=1, ctx=ctx)
+    T, k_r = 40, 6
+    outs = nl.nlem_denoise_batch(imgs, [k for *_, k, S in specs], [S for *_, S in specs],
+                                 [10 * s for _, _, s, _, _ in specs], rho=0.7, iters=T, ctx=ctx,
+                                 solver=nl.SOLVER_FAST, restart_every=k_r)
+    cfg = nl.nlem_batch_config(ctx)
+    assert cfg.startswith("accelerated")
+    if forced == 1:
+        assert "by window" in cfg
+    for i, ((H, W, s, k, S), g) in enumerate(zip(specs, imgs_h)):
+        ref = oracle.nlem(g, k, S, 10 * s, 0.7, T, fast=True, restart_every=k_r)
+        err = rel_err(outs[i]["out"].cpu().numpy(), ref["out"])
+        assert err.max() <= TOL, (i, err.max())
+        assert np.all(outs[i]["iters_used"].cpu().numpy() == T)
+
+
+def test_batch_accelerated_rho1_stops_by_the_rule(nl):
+    """At rho = 1 (tolerance 1e-4 every 10 iterations, cap 300) Algorithm 1 reaches the cap on almost
+    every pixel.  The accelerated batch stops pixels by the rule, each at a check point with its
+    residual below the tolerance, as often as the oracle's accelerated solver does on a sample of the
+    same pixels (these small images are hard: the oracle stops 53-72% of them)."""
+    specs = [(48, 64, 20.0, 7, 21), (40, 40, 10.0, 5, 15), (56, 32, 40.0, 7, 11)]
+    imgs_h = [synth.noisy_image(3700 + i, H, W, s)[0] for i, (H, W, s, k, S) in enumerate(specs)]
+    imgs = [torch.from_numpy(g).to(DEV) for g in imgs_h]
+    args = ([k for *_, k, S in specs], [S for *_, S in specs], [10 * s for _, _, s, _, _ in specs])
+    fast = nl.nlem_denoise_batch(imgs, *args, rho=1.0, iters=300, tol=1e-4, check_every=10, solver=nl.SOLVER_FAST)
+    plain = nl.nlem_denoise_batch(imgs, *args, rho=1.0, iters=300, tol=1e-4, check_every=10)
+    used = np.concatenate([o["iters_used"].cpu().numpy().reshape(-1) for o in fast])
+    res = np.concatenate([o["residual"].cpu().numpy().reshape(-1) for o in fast])
+    used_plain = np.concatenate([o["iters_used"].cpu().numpy().reshape(-1) for o in plain])
+    assert np.all((used % 10 == 0) | (used == 300))
+    assert np.all(res[used < 300] < 1e-4)
+    got, ref = [], []
+    for (H, W, s, k, S), g, o in zip(specs, imgs_h, fast):
+        pix = np.arange(0, H * W, 5)
+        r = oracle.nlem(g, k, S, 10 * s, 1.0, 300, tol=1e-4, check_every=10, pixels=pix, fast=True)
+        ref.append(r["iters_used"] < 300)
+        got.append(o["iters_used"].cpu().numpy().reshape(-1)[pix] < 300)
+    got, ref = np.concatenate(got), np.concatenate(ref)
+    assert abs(got.mean() - ref.mean()) <= 0.1, (got.mean(), ref.mean())
+    assert got.mean() >= np.mean(used_plain < 300) + 0.4
+
+
 def test_batch_rejects_unsupported(nl):
     g = torch.zeros((20, 20), device=DEV)
     with pytest.raises(nl.NlemError) as e:
@@ -120,4 +173,7 @@ def test_batch_rejects_unsupported(nl):
     assert e.value.code == -5
     with pytest.raises(nl.NlemError) as e:
         nl.nlem_denoise_batch([g], [4], [11], [100.0])
+    assert e.value.code == -1
+    with pytest.raises(nl.NlemError) as e:   # IRLS is nlem_denoise's only
+        nl.nlem_denoise_batch([g], [7], [11], [100.0], solver=nl.SOLVER_IRLS)
     assert e.value.code == -1
