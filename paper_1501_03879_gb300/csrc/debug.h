@@ -19,6 +19,8 @@ enum DebugSite : int {
   kDbgPairTile = 5,       // pixel pairs: tile store or load
   kDbgPairRow = 6,        // pixel pairs: point-row store
   kDbgBatchItem = 7,      // batched launch: item -> image lookup
+  kDbgFastVec = 8,        // accelerated solver: a finalize lane's pair of d-vector slots
+  kDbgFastPartial = 9,    // accelerated solver: a per-warp partial column sum
 };
 
 struct DebugRecord {

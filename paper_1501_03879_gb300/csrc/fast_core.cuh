@@ -43,6 +43,7 @@
 #pragma once
 
 #include "admm_core.cuh"
+#include "debug.h"
 
 namespace nlemk {
 
@@ -218,8 +219,9 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
       float k = (b1 ? k1 : k0) + __shfl_xor_sync(kFull, b1 ? k0 : k1, H2);
 #pragma unroll
       for (int o = H2 / 2; o >= 1; o >>= 1) k += __shfl_xor_sync(kFull, k, o);
-      if ((lane & (H2 - 1)) == 0)
-        reinterpret_cast<float*>(sm.cred)[(warp * C::COLS + g * C::NQR + i) * 4 + (b2 ? 2 : 0) + (b1 ? 1 : 0)] = k;
+      const int ci = (warp * C::COLS + g * C::NQR + i) * 4 + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+      if ((lane & (H2 - 1)) == 0 && NLEM_DBG_OK(ci, C::NW * C::COLS * 4, kDbgFastPartial))
+        reinterpret_cast<float*>(sm.cred)[ci] = k;
     }
   }
 }
@@ -268,7 +270,8 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   const int col = lane >> 1, hh = lane & 1;
   const bool colok = col < C::COLS;
   const int sg = colok ? col / C::NQR : 0, quad = colok ? col - sg * C::NQR : 0;
-  const bool has = colok && quad < C::NQA;       // the pair lies in the d-vectors
+  const bool has = colok && quad < C::NQA &&     // the pair lies in the d-vectors
+                   NLEM_DBG_OK(sg * C::QA + 4 * quad + 2 * hh + 1, C::VEC, kDbgFastVec);
   const int real = slice_real<C>(sg, d);
   const int slot0 = 4 * quad + 2 * hh;
   const int vi = sg * C::QA + slot0;

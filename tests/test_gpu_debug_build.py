@@ -1,5 +1,6 @@
-"""The debug build (libnlem_debug.so: -DNLEM_DEBUG, bounds-checked tile, image, point-row and
-work-item indices) on small cases of every NLEM kernel family against the FP64 oracle, with its
+"""The debug build (libnlem_debug.so: -DNLEM_DEBUG, bounds-checked tile, image, point-row,
+work-item and accelerated-solver indices) on small cases of every NLEM kernel family and of the
+accelerated solver against the FP64 oracle, with its
 bounds-check record read back: no index may leave what it indexes.  It runs in a process of its
 own, which loads the debug library in place of the release one."""
 import os
@@ -49,6 +50,25 @@ pts = synth.em_points(61, np.arange(3), 300, 49)
 w = synth.em_weights(61, np.arange(3), 300)
 x = nl.em_solve_batch(torch.from_numpy(pts).to(dev), torch.from_numpy(w).to(dev), rho=0.5, iters=15)["x"]
 worst = max(worst, rel(x.cpu().numpy(), oracle.em_admm_batch(pts, w, 0.0, 255.0, 0.5, 15)[0]))
+# the accelerated solver on a fixed restart period (its schedule does not depend on rounding): NLEM one
+# pixel per CTA, both batch variants (5x5 and 7x7) and a standalone batch
+g, _ = synth.noisy_image(6200, 23, 31, 20.0)
+r = nl.nlem_denoise(torch.from_numpy(g).to(dev), patch=7, window=21, h=200.0, rho=0.5, iters=12,
+                    solver=nl.SOLVER_FAST, restart_every=4)
+worst = max(worst, rel(r["out"].cpu().numpy(), oracle.nlem(g, 7, 21, 200.0, 0.5, 12, fast=True, restart_every=4)["out"]))
+for v in (0, 1):
+    ctx = nl.Context(0)
+    nl.nlem_batch_force_config(v, fetch=4, ctas_per_sm=1, ctx=ctx)
+    outs = nl.nlem_denoise_batch([torch.from_numpy(g).to(dev) for g in imgs], [k for *_, k, S in specs],
+                                 [S for *_, S in specs], [300.0] * 3, rho=0.5, iters=10, ctx=ctx,
+                                 solver=nl.SOLVER_FAST, restart_every=3)
+    for (H, W, k, S), g, o in zip(specs, imgs, outs):
+        ref = oracle.nlem(g, k, S, 300.0, 0.5, 10, fast=True, restart_every=3)["out"]
+        worst = max(worst, rel(o["out"].cpu().numpy(), ref))
+x = nl.em_solve_batch(torch.from_numpy(pts).to(dev), torch.from_numpy(w).to(dev), rho=0.5, iters=15,
+                      solver=nl.SOLVER_FAST, restart_every=5)["x"]
+worst = max(worst, rel(x.cpu().numpy(), oracle.em_admm_batch(pts, w, 0.0, 255.0, 0.5, 15, fast=True,
+                                                             restart_every=5)[0]))
 st = nl.nlem_debug_status()
 print("DEBUG", st["count"], st["site"], st["index"], st["limit"], worst)
 """
