@@ -124,10 +124,10 @@ PROFILED = {
                          "issue_pct": 45.77, "smem_wavefront_pct": 41.38},
     "em_batch_kernel": {"sources": "ce399dc74d7e2592", "traffic": (362494976 + 3801856) * 64, "fma_pipe_pct": 40.76,
                         "issue_pct": 34.87, "smem_wavefront_pct": 65.80},
-    "nlem_kernel_fast": {"sources": "781b979d1ba86f9a", "traffic": (145408 + 0) * 16, "fma_pipe_pct": 33.66,
-                         "issue_pct": 33.55, "smem_wavefront_pct": 41.39},
-    "em_batch_kernel_fast": {"sources": "781b979d1ba86f9a", "traffic": (361447424 + 3664640) * 64,
-                             "fma_pipe_pct": 31.90, "issue_pct": 32.11, "smem_wavefront_pct": 39.34},
+    "nlem_kernel_fast": {"sources": "fe318b655c14afc8", "traffic": (144384 + 0) * 16, "fma_pipe_pct": 31.67,
+                         "issue_pct": 31.62, "smem_wavefront_pct": 41.03},
+    "em_batch_kernel_fast": {"sources": "fe318b655c14afc8", "traffic": (362551040 + 4095488) * 64,
+                             "fma_pipe_pct": 31.90, "issue_pct": 32.11, "smem_wavefront_pct": 39.29},
 }
 
 

@@ -413,9 +413,66 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
   }
 }
 
+// The norms ||e_k|| of this lane's points (sums of its slices' partial squares s), the factors
+// f_k = min(1, lam_k / ||e_k||) and gs = the lane's share of sum_k ||g_k||^2 = sum_k f_k^2 ||e_k||^2.
+// SCATTER (shapes with G = 4 slices on lanes xor 8 / xor 16 and P = 7): the 4 lanes of a point group
+// reduce-scatter the 7 sums so that each forms f for 2 points only, then gather the f values back
+// (fewer shuffles and reciprocal square roots than a full all-reduce per point).
+template <class C, bool SCATTER>
+__device__ __forceinline__ void fast_norms(const Smem<C>& sm, int g, int pg, float (&s)[C::P], float (&f)[C::P],
+                                           float& gs) {
+  gs = 0.f;
+  if constexpr (SCATTER && C::G == 4 && C::LPG == 8 && C::P == 7) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    // after the xor-16 and xor-8 halvings lane (b4, b3) holds points 4*b4 + 2*b3 + {0, 1} (the 8th a pad)
+    float k4[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const float lo = s[jj], hi = jj + 4 < C::P ? s[jj + 4] : 0.f;
+      k4[jj] = (b4 ? hi : lo) + __shfl_xor_sync(kFull, b4 ? lo : hi, 16);
+    }
+    float fo[2];
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const float r2 = (b3 ? k4[jj + 2] : k4[jj]) + __shfl_xor_sync(kFull, b3 ? k4[jj] : k4[jj + 2], 8);
+      const int idx = (b4 ? 4 : 0) + (b3 ? 2 : 0) + jj;
+      const bool real = idx < C::P;
+      // r2 = 0 gives lam*inf (or NaN when lam = 0) and fminf then yields 1, harmless because e = 0 there
+      const float lam = real ? sm.lam[pg + (real ? idx : 0) * C::NG] : 0.f;
+      fo[jj] = fminf(1.f, lam * rsqrtf(r2));
+      if (real) gs = fmaf(fo[jj] * fo[jj], r2, gs);   // each point counted once, by the lane that owns it
+    }
+    float f4[4];
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const float other = __shfl_xor_sync(kFull, fo[jj], 8);
+      f4[jj] = b3 ? other : fo[jj];
+      f4[jj + 2] = b3 ? fo[jj] : other;
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const float other = __shfl_xor_sync(kFull, f4[jj], 16);
+      f[jj] = b4 ? other : f4[jj];
+      if (jj + 4 < C::P) f[jj + 4] = b4 ? f4[jj] : other;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < C::P; ++k) s[k] = point_sum<C>(s[k]);
+#pragma unroll
+    for (int k = 0; k < C::P; ++k) {
+      const float r2 = s[k];
+      // r2 = 0 gives lam*inf (or NaN when lam = 0) and fminf then yields 1, harmless because e = 0 there
+      f[k] = fminf(1.f, sm.lam[pg + k * C::NG] * rsqrtf(r2));
+      gs = fmaf(f[k] * f[k], r2, gs);
+    }
+    if (g != 0) gs = 0.f;   // each point's ||g_k||^2 counted once, by its slice-0 lane
+  }
+}
+
 // One step with bank L = h(t-1) (latest) and O = h(t-2) (older, overwritten by h(t)).  Returns true
 // when the solve ends after this step.
-template <class C>
+template <class C, bool SCATTER>
 __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& fv, int n, int d, int it,
                                           const SolveParams& prm, int restart_every, float inv_n, float fn,
                                           const float2 (&L2)[C::P][C::Q / 2], const float (&L1)[C::P],
@@ -427,20 +484,9 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
   const float p = pq.y, q = pq.z;
   float s[C::P];
   fast_phase1<C>(sm, g, last, p, q, L2, L1, O2, O1, s);
-#pragma unroll
-  for (int k = 0; k < C::P; ++k) s[k] = point_sum<C>(s[k]);
   float f[C::P];
-  float gs = 0.f;
-#pragma unroll
-  for (int k = 0; k < C::P; ++k) {
-    const int j = pg + k * C::NG;
-    const float r2 = s[k];
-    // f = min(1, lam / ||e||); r2 = 0 gives lam*inf (or NaN when lam = 0) and fminf then yields 1,
-    // harmless because e = 0 there
-    f[k] = fminf(1.f, sm.lam[j] * rsqrtf(r2));
-    gs = fmaf(f[k] * f[k], r2, gs);
-  }
-  if (g != 0) gs = 0.f;   // each point's ||g_k||^2 counted once, by its slice-0 lane
+  float gs;
+  fast_norms<C, SCATTER>(sm, g, pg, s, f, gs);
   const float w2 = check ? fast_check_w2<C>(sm, fv, g, pg, last, f, n, O2, O1) : 0.f;
   fast_phase2<C>(sm, g, pg, last, f, w2, gs, O2, O1);
   __syncthreads();
@@ -457,7 +503,7 @@ __device__ __forceinline__ bool fast_step(const Smem<C>& sm, const FastVec<C>& f
 // Accelerated EM-ADMM from the state set up by the caller, as for admm_iterate: pts (rows of
 // -a_j, inactive slots zero), lam (w_j / mu), zv = cv = z(0) (phantom slots zero) and sgv = 0.
 // On return zv holds z; scal[2] = iterations run, scal[3] = last residual, scal[9] = restarts.
-template <class C>
+template <class C, bool SCATTER = false>
 __device__ void admm_fast_iterate(const Smem<C>& sm, const FastVec<C>& fv, int n, int d, const SolveParams& prm,
                                   int restart_every) {
   const int t = threadIdx.x, g = lane_slice<C>(), pg = lane_group<C>();
@@ -503,9 +549,9 @@ __device__ void admm_fast_iterate(const Smem<C>& sm, const FastVec<C>& fv, int n
   if (prm.iters > 0) {
     for (;;) {
       ++it;
-      if (fast_step<C>(sm, fv, n, d, it, prm, restart_every, inv_n, fn, hA, hA1, hB, hB1, R)) break;
+      if (fast_step<C, SCATTER>(sm, fv, n, d, it, prm, restart_every, inv_n, fn, hA, hA1, hB, hB1, R)) break;
       ++it;
-      if (fast_step<C>(sm, fv, n, d, it, prm, restart_every, inv_n, fn, hB, hB1, hA, hA1, R)) break;
+      if (fast_step<C, SCATTER>(sm, fv, n, d, it, prm, restart_every, inv_n, fn, hB, hB1, hA, hA1, R)) break;
     }
   }
   if (t == 0) {

@@ -138,9 +138,11 @@ __device__ __forceinline__ int reflect_idx(int x, int N) {
 // IRLS: the surrogate solver of Eq. 2 in place of EM-ADMM (NLEM-IRLS, the comparison method of
 // Sec. 3).  WPEN: EM-ADMM with per-point penalties mu_k = mu w_k (admm_iterate).  NEG: the point
 // rows hold -a_j (admm_core.cuh).  FAST: accelerated EM-ADMM (admm_fast_iterate, rows of -a_j, its
-// d-vectors after the carve: the launch adds FastVec<C>::BYTES of shared memory).  Ends with a
-// barrier, so the caller may start the next pixel at once.
-template <class C, int K, bool IRLS = false, bool WPEN = false, bool NEG = false, bool FAST = false>
+// d-vectors after the carve: the launch adds FastVec<C>::BYTES of shared memory; SCATTER: its
+// point norms by reduce-scatter, fast_norms).  Ends with a barrier, so the caller may start the next
+// pixel at once.
+template <class C, int K, bool IRLS = false, bool WPEN = false, bool NEG = false, bool FAST = false,
+          bool SCATTER = false>
 __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, int W, int pitch, int S,
                            float inv_h2, double ih2, const SolveParams& prm, int init_mode, long long pix,
                            float* __restrict__ out, int* __restrict__ iters_used, float* __restrict__ resid,
@@ -280,7 +282,7 @@ __device__ void nlem_pixel(Smem<C>& sm, const float* __restrict__ img, int H, in
   if constexpr (IRLS)
     irls_iterate<C, NEG>(sm, n, C::D, pp);
   else if constexpr (FAST)
-    admm_fast_iterate<C>(sm, FastVec<C>(sm.pts + C::TOTAL), n, C::D, pp, pp.restart_every);
+    admm_fast_iterate<C, SCATTER>(sm, FastVec<C>(sm.pts + C::TOTAL), n, C::D, pp, pp.restart_every);
   else
     admm_iterate<C, false, NoExchange, ScalarBox, WPEN, NEG>(sm, n, C::D, pp);
   if (ex.z_out) {
@@ -329,10 +331,11 @@ nlem_kernel(const float* __restrict__ img, int H, int W, int pitch, int S, float
     const long long pix = pix_list ? (long long)pix_list[it] : it;
     // rows of -a_j for the 7-point EM-ADMM shapes of 7x7 patches, measured 3% faster that way (the
     // 4-point shape measured 18% slower and the 9x9 one 0.5%, so the others keep rows of a_j); the
-    // accelerated solver always reads rows of -a_j
+    // accelerated solver always reads rows of -a_j.  Its norms by reduce-scatter measured 1.2% faster
+    // here; in the standalone batch and the batched launch they raised register spills and were slower
     constexpr bool kNeg = FAST || (C::P >= 7 && C::D == 49 && !IRLS);
-    nlem_pixel<C, K, IRLS, WPEN, kNeg, FAST>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix, out,
-                                             iters_used, resid, obj64, kkt64, wtab, ex);
+    nlem_pixel<C, K, IRLS, WPEN, kNeg, FAST, FAST>(sm, img, H, W, pitch, S, inv_h2, ih2, prm, init_mode, pix,
+                                                   out, iters_used, resid, obj64, kkt64, wtab, ex);
   }
 }
 
