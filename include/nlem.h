@@ -320,8 +320,7 @@ int nlem_batch_force_config(nlem_ctx* ctx, int variant, int fetch, int ctas_per_
  *   - Each call looks up the array's device address in the current context
  *     (cudaGetSymbolAddress, which allocates nothing), so the address stays right after
  *     cudaDeviceReset or under a caller's own driver-API context.  The first call in a context
- *     also loads the library's device code there: make that first call before any stream
- *     capture on that device.
+ *     also loads the library's device code there.
  *   - Every call shares the one array: the descriptors are rewritten and the counter is reset
  *     on each call, so calls whose GPU work overlaps (different streams, or different host
  *     threads, with no ordering between them) race and corrupt each other.  Order them.
