@@ -226,7 +226,6 @@ __device__ __forceinline__ void fast_phase2(const Smem<C>& sm, int g, int pg, bo
   }
 }
 
-// Warp 0 state of the momentum / restart rule, identical in every lane.
 // Warp 0 state of the momentum / restart rule, identical in every lane.  The countdowns to the next
 // periodic check and the next fixed-period restart (in place of a remainder per iteration) live in
 // shared memory, scal[6] and scal[7] as integers.
@@ -252,7 +251,9 @@ __device__ __forceinline__ void fast_zstep(float zh, float A, float inv_n, float
 // sum_k w~_k = n D(t-1) - sum_k u^_k - G.  The iterate's step s = z(t) - z(t-1) is carried exactly as
 // s = dl - D, dl = z^(t) - z(t-1) being beta s (momentum) or -s (restart) of the step before.
 // CHECK: a check iteration (residuals and the stopping test); the instance without them carries none of
-// their code, which otherwise lengthens the step's critical path.
+// their code, which otherwise lengthens the step's critical path.  The next-step vectors of both outcomes
+// (momentum and restart) are formed before the decision's warp sum and selected after it: the finalize
+// is one warp's dependent chain, and this takes them off it.
 template <class C, bool CHECK>
 __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C>& fv, int d, int it, float inv_n,
                                               float fn, const SolveParams& prm, int restart_every, FastRule& R) {
@@ -325,6 +326,24 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
       p_gs += A;
     }
   }
+  // both outcomes' next-step vectors, formed before the decision so that they overlap its warp sum
+  const float bpm = 1.f + beta_m;
+  float zhm[2], cnm[2], uhm[2], dlm[2], zhr[2], cnr[2], uhr[2], dlr[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float A = i ? A1 : A0;
+    const float zo = i ? zo2.y : zo2.x, Do = i ? do2.y : do2.x, Go = i ? go2.y : go2.x;
+    const float st = (i ? dl2.y : dl2.x) - D[i];   // z(t) - z(t-1)
+    const float uo = fmaf(fn, Do, -Go);
+    zhm[i] = fmaf(beta_m, st, z[i]);
+    cnm[i] = fmaf(beta_m, Do, fmaf(-bpm, D[i], zhm[i]));
+    uhm[i] = fmaf(bpm, fmaf(fn, D[i], -A), -beta_m * uo);
+    dlm[i] = beta_m * st;
+    zhr[i] = zo;
+    cnr[i] = zo - Do;
+    uhr[i] = uo;
+    dlr[i] = -st;
+  }
   p_DD = warp_sum(p_DD);
   const float cc = fn * p_DD;   // the z-part of the combined residual, divided by mu
   bool stop = false;
@@ -372,25 +391,13 @@ __device__ __forceinline__ void fast_finalize(const Smem<C>& sm, const FastVec<C
     float zhn[2], zrn[2], cn[2], uhn[2], dln[2], gn[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      zhn[i] = zrn[i] = cn[i] = uhn[i] = dln[i] = gn[i] = 0.f;
-      if (slot0 + i < real) {
-        const float A = i ? A1 : A0;
-        const float zo = i ? zo2.y : zo2.x, Do = i ? do2.y : do2.x, Go = i ? go2.y : go2.x;
-        const float st = (i ? dl2.y : dl2.x) - D[i];   // z(t) - z(t-1)
-        if (mom) {
-          zhn[i] = fmaf(beta, st, z[i]);
-          cn[i] = fmaf(beta, Do, fmaf(-bp, D[i], zhn[i]));
-          uhn[i] = fmaf(bp, fmaf(fn, D[i], -A), -beta * fmaf(fn, Do, -Go));
-          dln[i] = beta * st;
-        } else {
-          zhn[i] = zo;
-          cn[i] = zo - Do;
-          uhn[i] = fmaf(fn, Do, -Go);
-          dln[i] = -st;
-        }
-        zrn[i] = zhn[i] - D[i];
-        gn[i] = A;
-      }
+      const bool ok = slot0 + i < real;
+      zhn[i] = ok ? (mom ? zhm[i] : zhr[i]) : 0.f;
+      cn[i] = ok ? (mom ? cnm[i] : cnr[i]) : 0.f;
+      uhn[i] = ok ? (mom ? uhm[i] : uhr[i]) : 0.f;
+      dln[i] = ok ? (mom ? dlm[i] : dlr[i]) : 0.f;
+      zrn[i] = ok ? zhn[i] - D[i] : 0.f;
+      gn[i] = ok ? (i ? A1 : A0) : 0.f;
     }
     *reinterpret_cast<float2*>(sm.zv + vi) = make_float2(z[0], z[1]);
     if (!stop) {
