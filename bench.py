@@ -124,10 +124,10 @@ PROFILED = {
                          "issue_pct": 45.77, "smem_wavefront_pct": 41.38},
     "em_batch_kernel": {"sources": "ce399dc74d7e2592", "traffic": (362494976 + 3801856) * 64, "fma_pipe_pct": 40.76,
                         "issue_pct": 34.87, "smem_wavefront_pct": 65.80},
-    "nlem_kernel_fast": {"sources": "fe318b655c14afc8", "traffic": (144384 + 0) * 16, "fma_pipe_pct": 31.67,
-                         "issue_pct": 31.62, "smem_wavefront_pct": 41.03},
-    "em_batch_kernel_fast": {"sources": "fe318b655c14afc8", "traffic": (362551040 + 4095488) * 64,
-                             "fma_pipe_pct": 31.90, "issue_pct": 32.11, "smem_wavefront_pct": 39.29},
+    "nlem_kernel_fast": {"sources": "8c5aa888fe3d01d9", "traffic": (166656 + 0) * 16, "fma_pipe_pct": 32.60,
+                         "issue_pct": 32.73, "smem_wavefront_pct": 42.49},
+    "em_batch_kernel_fast": {"sources": "8c5aa888fe3d01d9", "traffic": (361556992 + 3713024) * 64,
+                             "fma_pipe_pct": 32.84, "issue_pct": 33.33, "smem_wavefront_pct": 40.81},
 }
 
 
