@@ -246,7 +246,7 @@ __device__ __forceinline__ void fast_zstep(float zh, float A, float inv_n, float
 // Warp 0, after the block reduction of step `it`: z, the residuals on check iterations, the
 // momentum-or-restart decision and the next step's vectors; publishes the stop flag, p, q and the next
 // step's check flag.
-// Phase 2 measured w~_k = x_k - r against r = z^ - D(t-1), a close guess of z (D changes slowly), so
+// The check pass measured w~_k = x_k - r against r = z^ - D(t-1), a close guess of z (D changes slowly), so
 // that sum_k ||x_k - z||^2 = W2 + 2 (D - D(t-1)) . sum w~ + n ||D - D(t-1)||^2 keeps small terms, with
 // sum_k w~_k = n D(t-1) - sum_k u^_k - G.  The iterate's step s = z(t) - z(t-1) is carried exactly as
 // s = dl - D, dl = z^(t) - z(t-1) being beta s (momentum) or -s (restart) of the step before.
