@@ -530,6 +530,23 @@ def test_fast_admm_period_beyond_the_run_never_restarts():
     assert rk == 0 and re_ == 0 and np.array_equal(zk, ze)
 
 
+def test_fast_admm_hand_worked_example():
+    """Iterates of the accelerated method worked by hand (derivation in the golden file): with a fixed
+    period of 3 the first extrapolated step puts z at -0.125 - 0.625 beta, beta = (phi - 1) / alpha+,
+    which pins the momentum weight; under the residual rule the restarts at iterations 2-5 pin that c
+    is measured against the step's start z^ and that a restart resumes from the previous iterate."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "fast_admm_worked_example.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 11
+    pts = np.array([[0.0], [10.0]])
+    w = np.array([3.0, 1.0])
+    for period, it, z_ref, rest_ref in rows:
+        z, used, _, _, rest = oracle.em_admm_fast(pts, w, -10.0, 20.0, 1.0, int(it), restart_every=int(period))
+        assert used == int(it)
+        assert abs(z[0] - float(z_ref)) < 1e-14, (period, it, z[0], z_ref)
+        assert rest == int(rest_ref), (period, it, rest, rest_ref)
+
+
 def test_fast_admm_decision_margin_limits():
     """The decision margin (a diagnostic of how near the run came to deciding the other way) is
     +inf where no decision compares two finite residuals: one iteration, or a fixed period."""
