@@ -314,7 +314,9 @@ int nlem_batch_force_config(nlem_ctx* ctx, int variant, int fetch, int ctas_per_
  * method itself needs no allocation; this entry point only moves the batched launch's scratch
  * (its work-queue counter and image descriptors) into a fixed array that the library holds.
  *   - Makes no device (or heap) allocation and needs no nlem_ctx; runs on the current device
- *     and `stream`; images as for nlem_denoise_batch (patch 5 or 7, window^2 <= 441).
+ *     and `stream`; images and options as for nlem_denoise_batch (patch 5 or 7,
+ *     window^2 <= 441; Algorithm 1, or the accelerated solver with opt->solver =
+ *     NLEM_SOLVER_FAST and opt->restart_every).
  *   - At most NLEM_NOALLOC_MAX_IMAGES images per call (-1 above that).  The array
  *     (about 18 KB) stays resident on every GPU that loads the library until the process exits.
  *   - Each call looks up the array's device address in the current context

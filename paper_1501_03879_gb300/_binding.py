@@ -535,11 +535,12 @@ def nlem_batch_config(ctx: Context | None = None) -> str:
 
 
 def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iters=100, box=(0.0, 255.0), tol=0.0,
-                               check_every=1, init=INIT_WEIGHTED_MEAN):
+                               check_every=1, init=INIT_WEIGHTED_MEAN, solver=SOLVER_ADMM, restart_every=0):
     """nlem_denoise_batch without any device allocation: the caller supplies every output
     buffer (`outs`: one dict per image with out [H,W] and optionally iters_used, residual);
     the library uses its own fixed scratch array.  At most 256 images per call; calls whose GPU
-    work overlaps must not run concurrently (they share that array)."""
+    work overlaps must not run concurrently (they share that array).  solver and restart_every
+    as for nlem_denoise_batch."""
     import torch
     n = len(images)
     if not (len(patches) == len(windows) == len(hs) == len(outs) == n):
@@ -561,7 +562,7 @@ def nlem_denoise_batch_noalloc(images, patches, windows, hs, outs, rho=1.0, iter
         d.residual = _ptr(outs[k]["residual"]).value if outs[k].get("residual") is not None else None
         d.H, d.W, d.pitch = H, W, pitch
         d.patch, d.window, d.h = int(patches[k]), int(windows[k]), float(hs[k])
-    o = _options(tol, check_every, PREC_FP32, init)
+    o = _options(tol, check_every, PREC_FP32, init, solver=solver, restart_every=restart_every)
     with torch.cuda.device(dev):   # the library runs on the current device: make it the images'
         _check(load_library().nlem_denoise_batch_noalloc(descs, n, float(rho), int(iters), _Box(*box),
                                                          ctypes.byref(o), _stream(dev)))

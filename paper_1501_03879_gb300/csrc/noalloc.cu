@@ -60,7 +60,11 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
       return nerr(NLEM_ERR_INVALID, "unknown layout");
     if (opt->penalty != NLEM_PENALTY_UNIFORM && opt->penalty != NLEM_PENALTY_WEIGHTED)
       return nerr(NLEM_ERR_INVALID, "unknown penalty");
-    if (opt->solver != NLEM_SOLVER_ADMM) return nerr(NLEM_ERR_INVALID, "the batched kernel runs EM-ADMM only");
+    if (opt->solver != NLEM_SOLVER_ADMM && opt->solver != NLEM_SOLVER_IRLS && opt->solver != NLEM_SOLVER_FAST)
+      return nerr(NLEM_ERR_INVALID, "unknown solver");
+    if (opt->restart_every < 0) return nerr(NLEM_ERR_INVALID, "restart_every must be >= 0");
+    if (opt->solver == NLEM_SOLVER_IRLS)
+      return nerr(NLEM_ERR_INVALID, "the batched kernel runs EM-ADMM only (plain or accelerated), not IRLS");
     if (opt->penalty != NLEM_PENALTY_UNIFORM)
       return nerr(NLEM_ERR_UNSUPPORTED, "the batched kernel takes one penalty for every point only");
     if (opt->precision != NLEM_PREC_FP32)
@@ -134,6 +138,8 @@ extern "C" int nlem_denoise_batch_noalloc(const nlem_image_desc* images, int cou
   L.prm.iters = iters;
   L.prm.tol = opt ? opt->tol : 0.f;
   L.prm.check_every = opt ? opt->check_every : 1;
+  L.prm.solver = opt ? opt->solver : NLEM_SOLVER_ADMM;   // Algorithm 1 or the accelerated solver
+  L.prm.restart_every = opt ? opt->restart_every : 0;
   L.prm.d = 0;
   L.init_mode = opt ? opt->init : NLEM_INIT_WEIGHTED_MEAN;
   L.sm_count = sms;

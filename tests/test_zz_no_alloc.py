@@ -120,8 +120,31 @@ def test_noalloc_error_codes_match_batch(nl):
     assert both(precision=nl.PREC_BF16) == (-5, -5)
     assert both(layout=7) == (-1, -1)
     assert both(solver=nl.SOLVER_IRLS) == (-1, -1)
+    assert both(solver=9) == (-1, -1)
+    assert both(solver=nl.SOLVER_FAST, restart_every=-1) == (-1, -1)
+    assert both(solver=nl.SOLVER_FAST, penalty=nl.PENALTY_WEIGHTED) == (-5, -5)
     assert both(check_every=0) == (-1, -1)
     assert both() == (0, 0)
+    assert both(solver=nl.SOLVER_FAST, restart_every=3) == (0, 0)
+
+
+def test_noalloc_accelerated_matches_batch(nl):
+    # the accelerated solver on a fixed restart period (a schedule that does not depend on
+    # rounding), 5x5 and 7x7 patches in one call, against nlem_denoise_batch
+    specs = [(27, 33, 20.0, 7, 21), (31, 22, 30.0, 5, 11), (19, 40, 40.0, 7, 13)]
+    ctx = nl.Context(0)
+    imgs, outs = _batch(5400, specs)
+    ks = [k for *_, k, S in specs]
+    Ss = [S for *_, S in specs]
+    hs = [10 * s for _, _, s, _, _ in specs]
+    nl.nlem_denoise_batch_noalloc(imgs, ks, Ss, hs, outs, rho=1.0, iters=40, solver=nl.SOLVER_FAST,
+                                  restart_every=5)
+    ref = nl.nlem_denoise_batch(imgs, ks, Ss, hs, rho=1.0, iters=40, ctx=ctx, solver=nl.SOLVER_FAST,
+                                restart_every=5)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o["iters_used"], r["iters_used"])
+        assert rel_err(o["out"].cpu().numpy(), r["out"].cpu().numpy()).max() <= TOL
 
 
 _RESET_CHILD = r"""
