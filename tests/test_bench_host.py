@@ -68,6 +68,21 @@ def test_irls_flop_count_follows_the_stated_convention():
     assert b.irls_flops(n, 4, d) == want
 
 
+def test_fast_flop_count_follows_the_stated_convention():
+    # 10 flops per element and iteration, 4 per point, 5 per element on each check iteration (the W2
+    # pass issues an FADD and two FFMAs per element); runs stop at check points or at the cap, so a
+    # run of t iterations checked every 10 has ceil(t / 10) check iterations
+    b = _bench()
+    n = np.array([[441.0, 121.0]])
+    it = np.array([[300.0, 20.0]])
+    d = 49
+    want = sum((10 * nn * d + 4 * nn) * t + 5 * nn * d * c + 5 * nn * d + 3 * nn
+               for nn, t, c in [(441, 300, 30), (121, 20, 2)])
+    assert b.fast_nlem_flops(n, it, d, 10) == want
+    assert b.fast_em_flops(np.array([90, 300, 7]), 441, 49, 10) == sum(
+        (10 * 441 * 49 + 4 * 441) * t + 5 * 441 * 49 * c + 2 * 441 * 49 for t, c in ((90, 9), (300, 30), (7, 1)))
+
+
 def test_profile_cases_are_the_documented_ones():
     b = _bench()
     import inspect
